@@ -1,0 +1,50 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case copies the oracle's C source, plants one mistake (a strict tie, a
+Theiler off-by-one, a wrong norm, a wrong vector count, dropped border or
+single-cell lines, a wrong log base, a wrong denominator, a missed longest
+line), builds the copy, and runs the pin suite against it in a subprocess:
+the suite must fail.  Everything runs on the CPU.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "rqa_oracle.c")
+
+MUTANTS = {
+    "strict_tie": ("st->norm) <= st->eps;", "st->norm) < st->eps;"),
+    "theiler_off_by_one": ("if (gap < (int64_t)st->theiler) return 0;",
+                           "if (gap <= (int64_t)st->theiler) return 0;"),
+    "l2_as_l1": ("acc = acc + diff * diff;", "acc = acc + fabs(diff);"),
+    "l1_without_abs": ("acc = acc + fabs(diff);", "acc = acc + diff;"),
+    "nvec_wrong": ("int64_t n = N - (int64_t)(m - 1) * (int64_t)tau;",
+                   "int64_t n = N - (int64_t)m * (int64_t)tau;"),
+    "drop_single_cells": ("if (len <= 0) return;", "if (len <= 1) return;"),
+    "drop_border_runs": ("  if (prev >= 0) close_run(hv, hw, prev, run);\n  return ones;",
+                         "  return ones;"),
+    "log2_entropy": ("acc = acc + p * log(p);", "acc = acc + p * log2(p);"),
+    "det_wrong_denominator": ("out->det = (double)d1 / (double)dall1;",
+                              "out->det = (double)d1 / (double)d0;"),
+    "lmax_misses_n": ("for (int64_t l = n; l >= lo; --l)",
+                      "for (int64_t l = n - 1; l >= lo; --l)"),
+    "tau_ignored": ("double b = s[j + (int64_t)k * tau];", "double b = s[j + (int64_t)k];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not found once: {old!r}"
+    mut = tmp_path / "rqa_oracle.c"
+    mut.write_text(src.replace(old, new))
+    env = dict(os.environ, RQA_ORACLE_SRC=str(mut))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
+    assert "failed" in r.stdout
