@@ -1,0 +1,231 @@
+/*
+ * rqa.h -- C ABI of the B300 (sm_103a) recurrence quantification analysis
+ * library (librqa_b300.so).
+ *
+ * The library computes, for a scalar time series, what the PyRQA paper
+ * describes as an RQA computation (Sect. 7, Listings 2-4):
+ *   1. time-delay embedding with dimension m and delay tau (Sect. 2, Sect. 7.2),
+ *   2. the binary recurrence matrix R_ij = [d(x_i, x_j) <= eps and |i-j| >= w]
+ *      under the L-infinity, L2 or L1 norm with a fixed radius eps
+ *      (Sect. 2, Sect. 7.2 "similarity measure" / FixedRadius) and a Theiler
+ *      window w, never materialised,
+ *   3. the frequency distributions of diagonal lines, vertical lines and white
+ *      vertical lines over the full n x n matrix (Sect. 2, the three line
+ *      types; Sect. 4.2, operators I-III), and
+ *   4. the measures of Table 3 (RR, DET, L, Lmax, DIV, L_entr, LAM, TT, Vmax,
+ *      V_entr) plus W, Wmax, W_entr for white vertical lines.
+ * n = N - (m-1)*tau embedded vectors x_i = (s[i], s[i+tau], ..., s[i+(m-1)tau]).
+ *
+ * Results are exact: every recurrence decision equals the FP64 decision
+ * d <= eps computed in the order
+ *   L1   d = ((|D0| + |D1|) + ...)      L2  d = sqrt(((D0*D0) + D1*D1) + ...)
+ *   Linf d = max_k |Dk|                 Dk = s[i+k*tau] - s[j+k*tau]
+ * with no fused multiply-add, so the histograms are integers that do not
+ * depend on the hardware, and the measures are computed from them on the
+ * host in a fixed order (see rqa_measures_t).
+ *
+ * Errors: every call returns an rqa_status (RQA_OK = 0); none aborts the
+ * process.  rqa_strerror() names a code; rqa_last_error() gives the detail of
+ * the last failure on a handle.  The library never falls back to the CPU:
+ * without a usable CUDA device, rqa_create() returns RQA_ENODEV.
+ *
+ * Threading: a handle is used by one thread at a time.  Server handles
+ * (rqa_server_*) are safe to call from several threads.
+ */
+#ifndef RQA_B300_H
+#define RQA_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+typedef enum {
+  RQA_OK = 0,
+  RQA_EINVAL = 1,    /* invalid settings or arguments                      */
+  RQA_ESHORT = 2,    /* fewer than one embedded vector (n < 1)             */
+  RQA_ENAN = 3,      /* a series value is NaN or infinite                  */
+  RQA_ENOMEM = 4,    /* device allocation failed or over the memory budget */
+  RQA_ECUDA = 5,     /* a CUDA call failed; see rqa_last_error()           */
+  RQA_ETIMEOUT = 6,  /* a bounded device-side wait gave up                 */
+  RQA_PENDING = 7,   /* server: the request has not finished yet           */
+  RQA_ENODEV = 8,    /* no CUDA device of compute capability 10.3          */
+  RQA_ETOOBIG = 9,   /* n or m beyond the supported maximum                */
+  RQA_ENOTFOUND = 10 /* server: unknown ticket                             */
+} rqa_status;
+
+typedef enum { RQA_NORM_MAX = 0, RQA_NORM_L2 = 1, RQA_NORM_L1 = 2 } rqa_norm;
+
+/* How pair distances are evaluated on the GPU.  Both give the same, exact
+ * result; they differ in speed.
+ *   RQA_PREC_AUTO / RQA_PREC_FP32_RECHECK: FP32 distances on centred, scaled
+ *     FP32 copies of the vectors; pairs whose FP32 margin |eps - d| (|eps^2 -
+ *     d^2| for L2) is within a proven error band are re-decided in FP64 with
+ *     the exact operation order above.
+ *   RQA_PREC_FP64: every pair in FP64 (the plain comparison path). */
+typedef enum {
+  RQA_PREC_AUTO = 0,
+  RQA_PREC_FP32_RECHECK = 1,
+  RQA_PREC_FP64 = 2
+} rqa_precision;
+
+/* Analysis parameters: the paper's Settings (Sect. 7.2, Listing 2). */
+typedef struct {
+  int32_t m;        /* embedding_dimension, 1..RQA_MAX_M                     */
+  int32_t tau;      /* time_delay, >= 1                                      */
+  double eps;       /* FixedRadius radius, finite and > 0                    */
+  int32_t norm;     /* rqa_norm (similarity_measure)                         */
+  int32_t theiler;  /* Theiler window w >= 0: cells with |i-j| < w are 0     */
+  int32_t l_min;    /* min_diagonal_line_length, >= 1                        */
+  int32_t v_min;    /* min_vertical_line_length, >= 1                        */
+  int32_t w_min;    /* min_white_vertical_line_length, >= 1                  */
+  int32_t precision;     /* rqa_precision                                    */
+  double band_override;  /* < 0: automatic band (exact).  >= 0: the FP32
+                            recheck band as a fraction of eps (of eps^2 for
+                            L2); +inf rechecks every pair.  A band below the
+                            proven bound may give inexact results, which
+                            rqa_stats_t.exact reports.                       */
+} rqa_settings;
+
+#define RQA_MAX_M 10
+#define RQA_MAX_N ((int64_t)1 << 22)
+
+/* Measures (the paper's RQAResult, Sect. 7.4, Table 3).  With P_D, P_V, P_W
+ * the histograms of diagonal, vertical and white vertical line lengths over
+ * the full matrix (line of identity included when w = 0) and RP the number
+ * of recurrence points:
+ *   rr = RP / (n*n)
+ *   det = sum_{l>=l_min} l P_D(l) / sum_{l>=1} l P_D(l)
+ *   l = sum_{l>=l_min} l P_D(l) / sum_{l>=l_min} P_D(l)
+ *   l_max = longest diagonal line >= l_min (0 if none), div = 1 / l_max
+ *   l_entr = 0 - sum_{l>=l_min, P_D(l)>0} p ln p, p = P_D(l) / sum_{l>=l_min} P_D,
+ *            accumulated in ascending l
+ *   lam, tt, v_max, v_entr: the same with P_V and v_min
+ *   w, w_max, w_entr: the same with P_W and w_min (no white analogue of det)
+ * Integer sums are exact (uint64); each quotient is one IEEE division, so
+ * 0/0 gives NaN and x/0 gives +inf.                                          */
+typedef struct {
+  double rr, det, l, div, l_entr, lam, tt, v_entr, w, w_entr;
+  int64_t l_max, v_max, w_max, n_vec, recurrence_points;
+} rqa_measures_t;
+
+/* Diagnostics of the last run on a handle (not part of the result). */
+typedef struct {
+  int64_t n_vec;
+  int64_t pairs;          /* unique off-window pairs i < j, j - i >= max(w,1) */
+  int64_t rechecks;       /* pairs re-decided in FP64                         */
+  double band;            /* recheck band used, in units of eps (eps^2 L2)    */
+  double band_bound;      /* proven sufficient band, same units               */
+  int32_t precision_used; /* rqa_precision actually run                       */
+  int32_t exact;          /* 1 if band >= band_bound (or FP64 path)           */
+  int32_t strip_width;    /* columns per CTA strip                            */
+  int32_t warps_per_cta;
+  int32_t cols_per_lane;
+  int32_t ctas;           /* persistent CTAs launched                         */
+  float kernel_ms;        /* device time of the tile kernel (events)          */
+  float total_ms;         /* device time of all kernels of the run            */
+} rqa_stats_t;
+
+typedef struct rqa_handle rqa_handle;
+
+/* Create a computation (RQAComputation.create, Sect. 7.3).  Validates the
+ * settings (RQA_EINVAL) and selects the current CUDA device (RQA_ENODEV if
+ * there is none of compute capability 10.3).  *out receives the handle. */
+int rqa_create(const rqa_settings* settings, rqa_handle** out);
+
+/* Run on a host series of n FP64 values (RQAComputation.run, Sect. 7.4).
+ * The library copies the series to the device (pageable or pinned host
+ * memory both work) and blocks until the result is ready.  Device buffers
+ * are owned by the handle and reused by later runs of the same or smaller n. */
+int rqa_run(rqa_handle* h, const double* host_series, int64_t n);
+
+/* Run on a series already on the device (e.g. a torch CUDA tensor), ordered
+ * on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
+ * caller keeps the series alive and unmodified until the call returns; the
+ * call returns when the results are on the host. */
+int rqa_run_device(rqa_handle* h, const double* dev_series, int64_t n,
+                   void* cuda_stream);
+
+/* Copy the measures of the last successful run. */
+int rqa_measures(const rqa_handle* h, rqa_measures_t* out);
+
+/* Copy a histogram of the last run: kind 0 = diagonal lines, 1 = vertical
+ * lines, 2 = white vertical lines; entry l = number of lines of length l,
+ * l = 0..n (entry 0 is always 0).  cap = capacity of `out` in entries;
+ * *len receives n + 1.  RQA_EINVAL if cap < n + 1 (then *len still says how
+ * many entries are needed). */
+int rqa_histogram(const rqa_handle* h, int32_t kind, uint64_t* out,
+                  int64_t cap, int64_t* len);
+
+int rqa_stats(const rqa_handle* h, rqa_stats_t* out);
+
+/* Evaluate individual recurrence decisions R_ij of the last run's series
+ * with the same device decision code as the tile kernel (FP32 test with the
+ * FP64 recheck band, or FP64).  i, j, out: host arrays of `count` entries;
+ * out[q] = R_{i[q], j[q]} (0 or 1).  For spot checks at sizes where the full
+ * matrix cannot be enumerated on the CPU. */
+int rqa_sample_decisions(rqa_handle* h, const int64_t* i, const int64_t* j,
+                         int64_t count, uint8_t* out);
+
+void rqa_destroy(rqa_handle* h);
+
+const char* rqa_strerror(int status);
+const char* rqa_last_error(const rqa_handle* h);
+
+/* ----------------------------------------------------------------- batched
+ * Many independent series in one submission: the work of all series is one
+ * queue of (series, strip) items processed by persistent CTAs, one launch
+ * per (m, norm) class, all launches captured in one CUDA graph that later
+ * calls with the same shapes replay.  settings[q] and series[q] (host
+ * pointers to lens[q] FP64 values) describe series q; out[q] receives its
+ * measures and status[q] its status.  The call returns RQA_OK if every
+ * series succeeded, else the first failing status. */
+typedef struct rqa_batch rqa_batch;
+
+int rqa_batch_create(rqa_batch** out);
+int rqa_batch_run(rqa_batch* b, const rqa_settings* settings,
+                  const double* const* series, const int64_t* lens,
+                  int32_t count, rqa_measures_t* out, int32_t* status);
+/* Histogram of series q of the last batch run (same layout as
+ * rqa_histogram). */
+int rqa_batch_histogram(const rqa_batch* b, int32_t q, int32_t kind,
+                        uint64_t* out, int64_t cap, int64_t* len);
+int rqa_batch_stats(const rqa_batch* b, rqa_stats_t* out);
+void rqa_batch_destroy(rqa_batch* b);
+
+/* ----------------------------------------------------------------- served
+ * Continuous batching.  Requests are admitted while their device memory
+ * (series, embedded vectors, descriptors, histograms) fits in
+ * mem_budget_bytes and a slot is free; admitted requests are batched into
+ * launch epochs as they arrive, so work of requests that arrive while others
+ * run overlaps on the device.  Each request keeps its own histograms and
+ * boundary state on the device until it completes. */
+typedef struct rqa_server rqa_server;
+
+int rqa_server_create(size_t mem_budget_bytes, int32_t max_slots,
+                      rqa_server** out);
+/* Copy the series and queue the request; *ticket identifies it. */
+int rqa_submit(rqa_server* s, const rqa_settings* settings,
+               const double* host_series, int64_t n, uint64_t* ticket);
+/* RQA_PENDING until done; then the request's status, with *out filled on
+ * RQA_OK.  A finished ticket may be polled until rqa_release(). */
+int rqa_poll(rqa_server* s, uint64_t ticket, rqa_measures_t* out);
+/* Block until the ticket finishes or timeout_ms passes (RQA_PENDING). */
+int rqa_wait(rqa_server* s, uint64_t ticket, int64_t timeout_ms,
+             rqa_measures_t* out);
+/* Forget a finished ticket, or cancel a queued one. */
+int rqa_release(rqa_server* s, uint64_t ticket);
+/* Server counters: admitted, completed, queued, in_flight, bytes_in_use,
+ * epochs (launches).  Any pointer may be NULL. */
+int rqa_server_counters(rqa_server* s, int64_t* admitted, int64_t* completed,
+                        int64_t* queued, int64_t* in_flight,
+                        int64_t* bytes_in_use, int64_t* epochs);
+void rqa_server_destroy(rqa_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RQA_B300_H */

@@ -1,0 +1,231 @@
+// rqa_api.cpp -- the extern "C" entry points of include/rqa.h for single
+// series (rqa_*) and batches (rqa_batch_*).  Argument checks and marshalling
+// only; all computation is in the engine's CUDA kernels.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/rqa.h"
+#include "rqa_engine.h"
+
+struct rqa_handle {
+  rqa_settings st{};
+  std::unique_ptr<rqa::Engine> eng;
+  rqa::SeriesResult res;
+  bool have = false;
+  std::string err;
+};
+
+struct rqa_batch {
+  std::unique_ptr<rqa::Engine> eng;
+  std::vector<rqa::SeriesResult> res;
+  rqa_stats_t stats{};
+  std::string err;
+};
+
+namespace {
+
+int find_device(int* dev, std::string* msg) {
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0) {
+    cudaGetLastError();
+    *msg = std::string("no CUDA device: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "count 0");
+    return RQA_ENODEV;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, cur);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, cur);
+  if (major != 10 || minor != 3) {
+    *msg = "current CUDA device is compute capability " + std::to_string(major) + "." +
+           std::to_string(minor) + "; this library is built for sm_103a (B300)";
+    return RQA_ENODEV;
+  }
+  *dev = cur;
+  return RQA_OK;
+}
+
+int copy_hist(const rqa::SeriesResult& r, int32_t kind, uint64_t* out, int64_t cap, int64_t* len) {
+  if (kind < 0 || kind > 2) return RQA_EINVAL;
+  const int64_t need = r.n + 1;
+  if (len) *len = need;
+  if (!out || cap < need) return RQA_EINVAL;
+  std::memcpy(out, r.hist.data() + kind * need, sizeof(uint64_t) * need);
+  return RQA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rqa_strerror(int status) {
+  switch (status) {
+    case RQA_OK: return "ok";
+    case RQA_EINVAL: return "invalid argument";
+    case RQA_ESHORT: return "series too short for the embedding";
+    case RQA_ENAN: return "series contains NaN or infinite values";
+    case RQA_ENOMEM: return "out of device memory or over the memory budget";
+    case RQA_ECUDA: return "CUDA error";
+    case RQA_ETIMEOUT: return "a bounded device-side wait gave up";
+    case RQA_PENDING: return "pending";
+    case RQA_ENODEV: return "no usable CUDA device (sm_103a)";
+    case RQA_ETOOBIG: return "size above the supported maximum";
+    case RQA_ENOTFOUND: return "unknown ticket";
+    default: return "unknown status";
+  }
+}
+
+int rqa_create(const rqa_settings* settings, rqa_handle** out) {
+  if (!out) return RQA_EINVAL;
+  *out = nullptr;
+  std::string msg;
+  int rc = rqa::validate_settings(settings, &msg);
+  if (rc != RQA_OK) return rc;
+  int dev = 0;
+  rc = find_device(&dev, &msg);
+  if (rc != RQA_OK) return rc;
+  rqa_handle* h = new (std::nothrow) rqa_handle();
+  if (!h) return RQA_ENOMEM;
+  h->st = *settings;
+  h->eng.reset(new (std::nothrow) rqa::Engine(dev));
+  if (!h->eng) {
+    delete h;
+    return RQA_ENOMEM;
+  }
+  *out = h;
+  return RQA_OK;
+}
+
+static int run_common(rqa_handle* h, const double* host, const double* dev, int64_t n,
+                      void* stream) {
+  if (!h) return RQA_EINVAL;
+  h->have = false;
+  h->err.clear();
+  if (!host && !dev) {
+    h->err = "series pointer is NULL";
+    return RQA_EINVAL;
+  }
+  std::vector<rqa::SeriesInput> in(1);
+  in[0].st = h->st;
+  in[0].host = host;
+  in[0].dev = dev;
+  in[0].N = n;
+  std::vector<rqa::SeriesResult> res;
+  int rc = h->eng->run(in, res, static_cast<cudaStream_t>(stream), false);
+  if (rc != RQA_OK) {
+    h->err = h->eng->error();
+    return rc;
+  }
+  h->res = std::move(res[0]);
+  h->have = true;
+  return RQA_OK;
+}
+
+int rqa_run(rqa_handle* h, const double* host_series, int64_t n) {
+  return run_common(h, host_series, nullptr, n, nullptr);
+}
+
+int rqa_run_device(rqa_handle* h, const double* dev_series, int64_t n, void* cuda_stream) {
+  return run_common(h, nullptr, dev_series, n, cuda_stream);
+}
+
+int rqa_measures(const rqa_handle* h, rqa_measures_t* out) {
+  if (!h || !out) return RQA_EINVAL;
+  if (!h->have) return RQA_EINVAL;
+  *out = h->res.meas;
+  return RQA_OK;
+}
+
+int rqa_histogram(const rqa_handle* h, int32_t kind, uint64_t* out, int64_t cap, int64_t* len) {
+  if (!h || !h->have) return RQA_EINVAL;
+  return copy_hist(h->res, kind, out, cap, len);
+}
+
+int rqa_stats(const rqa_handle* h, rqa_stats_t* out) {
+  if (!h || !out || !h->have) return RQA_EINVAL;
+  *out = h->res.stats;
+  return RQA_OK;
+}
+
+int rqa_sample_decisions(rqa_handle* h, const int64_t* i, const int64_t* j, int64_t count,
+                         uint8_t* out) {
+  if (!h || !h->have || count < 0 || (count > 0 && (!i || !j || !out))) return RQA_EINVAL;
+  int rc = h->eng->sample(i, j, count, out);
+  if (rc != RQA_OK) h->err = h->eng->error();
+  return rc;
+}
+
+void rqa_destroy(rqa_handle* h) { delete h; }
+
+const char* rqa_last_error(const rqa_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+// ------------------------------------------------------------------ batch
+int rqa_batch_create(rqa_batch** out) {
+  if (!out) return RQA_EINVAL;
+  *out = nullptr;
+  std::string msg;
+  int dev = 0;
+  int rc = find_device(&dev, &msg);
+  if (rc != RQA_OK) return rc;
+  rqa_batch* b = new (std::nothrow) rqa_batch();
+  if (!b) return RQA_ENOMEM;
+  b->eng.reset(new (std::nothrow) rqa::Engine(dev));
+  if (!b->eng) {
+    delete b;
+    return RQA_ENOMEM;
+  }
+  *out = b;
+  return RQA_OK;
+}
+
+int rqa_batch_run(rqa_batch* b, const rqa_settings* settings, const double* const* series,
+                  const int64_t* lens, int32_t count, rqa_measures_t* out, int32_t* status) {
+  if (!b || count < 0 || (count > 0 && (!settings || !series || !lens))) return RQA_EINVAL;
+  std::vector<rqa::SeriesInput> in(count);
+  for (int32_t q = 0; q < count; ++q) {
+    in[q].st = settings[q];
+    in[q].host = series[q];
+    in[q].N = lens[q];
+  }
+  int rc = b->eng->run(in, b->res, nullptr, true);
+  b->err = b->eng->error();
+  b->stats = rqa_stats_t{};
+  for (int32_t q = 0; q < count && q < static_cast<int32_t>(b->res.size()); ++q) {
+    if (status) status[q] = b->res[q].status;
+    if (out) {
+      if (b->res[q].status == RQA_OK)
+        out[q] = b->res[q].meas;
+      else
+        std::memset(&out[q], 0, sizeof(rqa_measures_t));
+    }
+    b->stats.n_vec += b->res[q].n;
+    b->stats.pairs += b->res[q].stats.pairs;
+    b->stats.rechecks += b->res[q].stats.rechecks;
+  }
+  b->stats.kernel_ms = b->eng->last_tile_ms();
+  b->stats.total_ms = b->eng->last_total_ms();
+  return rc;
+}
+
+int rqa_batch_histogram(const rqa_batch* b, int32_t q, int32_t kind, uint64_t* out, int64_t cap,
+                        int64_t* len) {
+  if (!b || q < 0 || q >= static_cast<int32_t>(b->res.size())) return RQA_EINVAL;
+  if (b->res[q].status != RQA_OK) return b->res[q].status;
+  return copy_hist(b->res[q], kind, out, cap, len);
+}
+
+int rqa_batch_stats(const rqa_batch* b, rqa_stats_t* out) {
+  if (!b || !out) return RQA_EINVAL;
+  *out = b->stats;
+  return RQA_OK;
+}
+
+void rqa_batch_destroy(rqa_batch* b) { delete b; }
+
+}  // extern "C"

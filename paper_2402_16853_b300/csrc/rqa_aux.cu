@@ -1,0 +1,347 @@
+// rqa_aux.cu -- the kernels around the fused tile kernel:
+//   prepare   per series: min / max / non-finite check, centring and power-
+//             of-two scaling for the FP32 copy, FP32 radius and the proven
+//             FP32 recheck band;
+//   embed     time-delay embedding (Sect. 2, Sect. 7.2) into FP32 vectors;
+//   merge     join the boundary descriptors of the CTA strips along every
+//             row and every diagonal (the carryover buffers of Sect. 4.1);
+//   finalize  join the runs of each full column at the line of identity and
+//             form the full diagonal histogram from the upper triangle;
+//   sample    individual decisions R_ij for spot checks.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rqa_internal.h"
+#include "rqa_kernels.h"
+#include "rqa_tile.cuh"
+
+namespace rqa {
+
+// ----------------------------------------------------------------- prepare
+__global__ void prepare_kernel(SeriesDesc* __restrict__ sd) {
+  SeriesDesc& S = sd[blockIdx.x];
+  __shared__ double s_mn[32], s_mx[32];
+  __shared__ int s_bad[32];
+  double mn = INFINITY, mx = -INFINITY;
+  int bad = 0;
+  for (int64_t i = threadIdx.x; i < S.N; i += blockDim.x) {
+    const double v = S.s[i];
+    if (!isfinite(v)) {
+      bad = 1;
+    } else {
+      mn = fmin(mn, v);
+      mx = fmax(mx, v);
+    }
+  }
+  // min, max and or are order-independent, so the reduction is deterministic
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = fmin(mn, __shfl_xor_sync(FULL, mn, o));
+    mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
+    bad |= __shfl_xor_sync(FULL, bad, o);
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    s_mn[wid] = mn;
+    s_mx[wid] = mx;
+    s_bad[wid] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < nw; ++w) {
+    mn = fmin(mn, s_mn[w]);
+    mx = fmax(mx, s_mx[w]);
+    bad |= s_bad[w];
+  }
+  mn = fmin(mn, s_mn[0]);
+  mx = fmax(mx, s_mx[0]);
+  bad |= s_bad[0];
+  if (bad) {
+    atomicExch(&S.counters[CNT_STATUS], 3ull /* RQA_ENAN */);
+    return;
+  }
+  // Centre on the mid-range (minimises max |s - c|) and scale by a power of
+  // two so the FP32 copies lie in [-1, 1].
+  const double center = 0.5 * mn + 0.5 * mx;
+  const double dev = fmax(mx - center, center - mn) * (1.0 + 0x1p-50);
+  double scale = 1.0;
+  if (dev > 0.0) scale = ldexp(1.0, -ilogb(dev) - 1);
+  double E = S.eps * scale;
+  if (!(E <= 0x1p20)) E = 0x1p20;  // every pair recurs by a huge margin
+  const double Ms = dev * scale;
+  const double u = 0x1p-24, m = (double)S.m, sm = sqrt(m);
+  double unit, bound;
+  // Bounds on |FP32 margin - exact margin| for the operation sequences of
+  // pair_margin(), from the rounding of the FP32 copies (<= u Ms each), of
+  // each subtraction, accumulation and of the radius, plus the rounding of
+  // the FP64 decision itself; doubled for the first-order terms' neglected
+  // higher orders.
+  if (S.norm == 1) {
+    const double a = 2.0 * u * Ms + u * E;
+    unit = E * E;
+    bound = 2.02 * ((3.0 + m + 2.0 * sm) * u * E * E + 2.0 * a * sm * E + m * a * a) +
+            (m + 3.0) * 0x1p-52 * E * E;
+  } else if (S.norm == 2) {
+    unit = E;
+    bound = 2.02 * ((1.0 + 2.0 * m) * u * E + 2.0 * m * u * Ms) + (m + 3.0) * 0x1p-52 * E;
+  } else {
+    unit = E;
+    bound = 2.02 * (3.0 * u * E + 2.0 * u * Ms) + 4.0 * 0x1p-52 * E;
+  }
+  double band = fmax(1e-5 * unit, bound);
+  if (S.band_override >= 0.0)
+    band = S.band_override * unit;
+  else if (bound >= 0.25 * unit)
+    band = INFINITY;  // the FP32 test would decide almost nothing: re-decide all
+  float thr;
+  if (S.norm == 1) {
+    const float e32 = __double2float_rn(E);
+    thr = __fmul_rn(e32, e32);
+  } else {
+    thr = __double2float_rn(E);
+  }
+  S.center = center;
+  S.scale = scale;
+  S.thr = thr;
+  S.band = __double2float_ru(band);
+  S.band_rel = band / unit;
+  S.bound_rel = bound / unit;
+}
+
+// ------------------------------------------------------------------- embed
+__global__ void embed_kernel(SeriesDesc* __restrict__ sd) {
+  const SeriesDesc& S = sd[blockIdx.y];
+  const int64_t total = S.n * S.mp;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = q / S.mp;
+    const int k = (int)(q - i * S.mp);
+    float v = 0.f;
+    if (k < S.m)
+      v = __double2float_rn(__dmul_rn(__dsub_rn(S.s[i + (int64_t)k * S.tau], S.center), S.scale));
+    S.xe[q] = v;
+  }
+}
+
+// ------------------------------------------------- block-level histograms
+struct BlockHist {
+  uint32_t* sh;   // [3][HB]
+  __device__ void init() {
+    for (int q = threadIdx.x; q < 3 * HB; q += blockDim.x) sh[q] = 0;
+    __syncthreads();
+  }
+  __device__ void add(const SeriesDesc& S, int type, uint64_t len) {
+    if (len < (uint64_t)HB && len > 0)
+      atomicAdd(&sh[type * HB + len], 1u);
+    else if (len > 0 && len <= (uint64_t)S.n)
+      atomicAdd(&S.hist[type * (S.n + 1) + len], 1ull);
+    else
+      atomicExch(&S.counters[CNT_STATUS], STATUS_INTERNAL);
+  }
+  __device__ void flush(const SeriesDesc& S) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < 3 * HB; q += blockDim.x) {
+      const uint32_t v = sh[q];
+      if (v) atomicAdd(&S.hist[(q / HB) * (S.n + 1) + (q % HB)], (unsigned long long)v);
+    }
+  }
+};
+
+__device__ __forceinline__ void emit2(BlockHist& h, const SeriesDesc& S, uint32_t col,
+                                      uint64_t len) {
+  if (len) h.add(S, col ? HIST_VERT : HIST_WHITE, len);
+}
+
+// ------------------------------------------------------------ merge: rows
+// Row i (cells (i, j), j > i) crosses strips Q = 0 .. (n-2-i)/sw from right
+// to left.  Each strip left a descriptor: the run touching its right edge
+// (a) and the run touching its left end (z), or one run over the whole
+// segment.  Join them in order; the run left open at column i+1 is the row's
+// end run for the line-of-identity join.
+__global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd) {
+  const SeriesDesc& S = sd[blockIdx.y];
+  __shared__ uint32_t sh[3 * HB];
+  BlockHist h{sh};
+  h.init();
+  const int64_t n = S.n, sw = S.sw;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n - 1;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t qlast = (n - 2 - i) / sw;
+    uint32_t ocol = 0;
+    uint64_t olen = 0;
+    for (int64_t Q = 0; Q <= qlast; ++Q) {
+      const int64_t off = strip_offset(n, sw, Q) + i;
+      const uint32_t z = S.row_z[off];
+      const uint32_t zlen = z >> 2, zcol = z & 1u;
+      if (z & 2u) {  // one run over the whole segment
+        if (olen && ocol == zcol) {
+          olen += zlen;
+        } else {
+          emit2(h, S, ocol, olen);
+          ocol = zcol;
+          olen = zlen;
+        }
+      } else {
+        const uint32_t a = S.row_a[off];
+        const uint32_t alen = a >> 1, acol = a & 1u;
+        if (olen && ocol == acol) {
+          emit2(h, S, acol, olen + alen);
+        } else {
+          emit2(h, S, ocol, olen);
+          emit2(h, S, acol, alen);
+        }
+        ocol = zcol;
+        olen = zlen;
+      }
+    }
+    S.rowend[i] = (uint32_t)olen | (ocol << 31);
+  }
+  h.flush(S);
+}
+
+// ------------------------------------------------------- merge: diagonals
+// Diagonal k >= 1 (cells (i, i+k)) starts at column n-1 and ends at (0, k):
+// it crosses strips Q = 0 .. (n-1-k)/sw.  Each strip left the black run
+// touching its entry (a), the black run touching its exit (z), or an
+// all-black flag.
+__global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd) {
+  const SeriesDesc& S = sd[blockIdx.y];
+  __shared__ uint32_t sh[3 * HB];
+  BlockHist h{sh};
+  h.init();
+  const int64_t n = S.n, sw = S.sw;
+  for (int64_t k = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t qlast = (n - 1 - k) / sw;
+    uint64_t L = 0;
+    for (int64_t Q = 0; Q <= qlast; ++Q) {
+      const int64_t off = strip_offset(n, sw, Q) + k - 1;
+      const uint32_t z = S.dia_z[off];
+      if (z & 0x8000u) {
+        L += (z & 0x7FFFu);
+      } else {
+        const uint64_t first = L + S.dia_a[off];
+        if (first) h.add(S, HIST_DIAG, first);
+        L = z & 0x7FFFu;
+      }
+    }
+    if (L) h.add(S, HIST_DIAG, L);
+  }
+  h.flush(S);
+}
+
+// ----------------------------------------------------------------- finalize
+// Full column j = upper column j (rows < j), the line-of-identity cell, and
+// upper row j (by symmetry).  The cell (j, j) is black iff w = 0.
+__global__ void join_loi_kernel(SeriesDesc* __restrict__ sd) {
+  const SeriesDesc& S = sd[blockIdx.y];
+  __shared__ uint32_t sh[3 * HB];
+  BlockHist h{sh};
+  h.init();
+  const uint32_t cd = S.w == 0 ? 1u : 0u;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < S.n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t up = S.colend[j], rt = S.rowend[j];
+    uint64_t L = 1;
+    const uint32_t ulen = up & 0x7FFFFFFFu, ucol = up >> 31;
+    const uint32_t rlen = rt & 0x7FFFFFFFu, rcol = rt >> 31;
+    if (ulen) {
+      if (ucol == cd) L += ulen; else emit2(h, S, ucol, ulen);
+    }
+    if (rlen) {
+      if (rcol == cd) L += rlen; else emit2(h, S, rcol, rlen);
+    }
+    emit2(h, S, cd, L);
+  }
+  h.flush(S);
+}
+
+// Full diagonal histogram: both triangles (symmetric) plus the line of
+// identity, one line of length n when w = 0.
+__global__ void diag_full_kernel(SeriesDesc* __restrict__ sd) {
+  const SeriesDesc& S = sd[blockIdx.y];
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l <= S.n;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long v = 2ull * S.hist[HIST_DIAG * (S.n + 1) + l];
+    if (S.w == 0 && l == S.n) v += 1ull;
+    S.hist[HIST_DIAG * (S.n + 1) + l] = v;
+  }
+}
+
+// ------------------------------------------------------------------ sample
+template <int NORM>
+__device__ bool sample_one(const SeriesDesc& S, int64_t i, int64_t j, bool f64) {
+  if (i > j) {
+    const int64_t t = i;
+    i = j;
+    j = t;
+  }
+  if (j - i < S.w) return false;
+  if (f64) return exact_decision<NORM>(S.s, i, j, S.m, S.tau, S.eps);
+  // FP32 margin in the tile kernel's order (row vector i, column vector j)
+  float acc;
+  if (NORM == 1) {
+    acc = S.thr;
+    for (int k = 0; k < S.m; ++k) {
+      const float d = __fsub_rn(S.xe[i * S.mp + k], S.xe[j * S.mp + k]);
+      acc = __fmaf_rn(-d, d, acc);
+    }
+  } else if (NORM == 2) {
+    acc = S.thr;
+    for (int k = 0; k < S.m; ++k)
+      acc = __fsub_rn(acc, fabsf(__fsub_rn(S.xe[i * S.mp + k], S.xe[j * S.mp + k])));
+  } else {
+    float mx = 0.f;
+    for (int k = 0; k < S.m; ++k)
+      mx = fmaxf(mx, fabsf(__fsub_rn(S.xe[i * S.mp + k], S.xe[j * S.mp + k])));
+    acc = __fsub_rn(S.thr, mx);
+  }
+  if (fabsf(acc) <= S.band) return exact_decision<NORM>(S.s, i, j, S.m, S.tau, S.eps);
+  return !(__float_as_uint(acc) >> 31);
+}
+
+__global__ void sample_kernel(const SeriesDesc* __restrict__ sd, const int64_t* __restrict__ ii,
+                              const int64_t* __restrict__ jj, int64_t count, uint8_t* out,
+                              int f64) {
+  const SeriesDesc& S = sd[0];
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = ii[q], j = jj[q];
+    bool r = false;
+    if (i >= 0 && j >= 0 && i < S.n && j < S.n) {
+      if (S.norm == 1) r = sample_one<1>(S, i, j, f64);
+      else if (S.norm == 2) r = sample_one<2>(S, i, j, f64);
+      else r = sample_one<0>(S, i, j, f64);
+    }
+    out[q] = r ? 1 : 0;
+  }
+}
+
+// ------------------------------------------------------------ host launch
+void launch_prepare(SeriesDesc* d_sd, int count, cudaStream_t st) {
+  prepare_kernel<<<count, 256, 0, st>>>(d_sd);
+}
+void launch_embed(SeriesDesc* d_sd, int count, int64_t max_n_mp, int sms, cudaStream_t st) {
+  int64_t blocks = (max_n_mp + 255) / 256;
+  if (blocks > 8 * sms) blocks = 8 * sms;
+  if (blocks < 1) blocks = 1;
+  embed_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+}
+void launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, int sms, cudaStream_t st) {
+  int64_t blocks = (max_n + 255) / 256;
+  if (blocks > 4 * sms) blocks = 4 * sms;
+  if (blocks < 1) blocks = 1;
+  merge_rows_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+  merge_diags_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+  join_loi_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+  diag_full_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+}
+void launch_sample(const SeriesDesc* d_sd, const int64_t* ii, const int64_t* jj, int64_t count,
+                   uint8_t* out, int f64, cudaStream_t st) {
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  if (blocks < 1) blocks = 1;
+  sample_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_sd, ii, jj, count, out, f64);
+}
+
+}  // namespace rqa

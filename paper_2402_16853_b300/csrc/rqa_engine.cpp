@@ -1,0 +1,581 @@
+// rqa_engine.cpp -- plans, launches and reads back one set of series.
+#include "rqa_engine.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <tuple>
+
+#include "rqa_kernels.h"
+
+namespace rqa {
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+int64_t nvec_of(const rqa_settings& st, int64_t N) {
+  return N - static_cast<int64_t>(st.m - 1) * st.tau;
+}
+
+// Unique off-window pairs i < j with j - i >= max(w, 1).
+int64_t pair_count(int64_t n, int w) {
+  const int64_t k0 = w < 1 ? 1 : w;
+  if (k0 > n - 1) return 0;
+  const int64_t cnt = n - k0;  // diagonals k0 .. n-1, lengths n-k0 .. 1
+  return cnt * (cnt + 1) / 2;
+}
+
+struct Sizes {
+  int64_t n = 0, nstrips = 0, ndesc = 0;
+  int mp = 0;
+  TileConfig tc{1, 4};
+  bool f64 = false;
+  size_t hist = 0, ends = 0, cnt = 0, desc = 0, series = 0, xe = 0;
+};
+
+Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series) {
+  Sizes z;
+  z.n = nvec_of(st, N);
+  z.f64 = st.precision == RQA_PREC_FP64;
+  z.mp = z.f64 ? 0 : ((st.m + 3) / 4) * 4;
+  z.tc = choose_tile(z.n, st.m, st.norm);
+  const int64_t sw = 32LL * z.tc.warps * z.tc.cols;
+  z.nstrips = num_strips(z.n, sw);
+  z.ndesc = strip_offset(z.n, sw, z.nstrips);
+  z.hist = align256(sizeof(uint64_t) * 3 * static_cast<size_t>(z.n + 1));
+  z.ends = align256(sizeof(uint32_t) * 2 * static_cast<size_t>(z.n));
+  z.cnt = align256(sizeof(uint64_t) * CNT_WORDS);
+  z.desc = 4 * align256(sizeof(uint16_t) * static_cast<size_t>(z.ndesc));
+  z.series = copy_series ? align256(sizeof(double) * static_cast<size_t>(N)) : 0;
+  z.xe = align256(sizeof(float) * static_cast<size_t>(z.n) * z.mp);
+  return z;
+}
+
+}  // namespace
+
+int validate_settings(const rqa_settings* st, std::string* msg) {
+  if (!st) {
+    *msg = "settings pointer is NULL";
+    return RQA_EINVAL;
+  }
+  if (st->m < 1) {
+    *msg = "embedding dimension m must be >= 1";
+    return RQA_EINVAL;
+  }
+  if (st->m > RQA_MAX_M) {
+    *msg = "embedding dimension m is above RQA_MAX_M (10)";
+    return RQA_ETOOBIG;
+  }
+  if (st->tau < 1) {
+    *msg = "time delay tau must be >= 1";
+    return RQA_EINVAL;
+  }
+  if (!std::isfinite(st->eps) || !(st->eps > 0.0)) {
+    *msg = "radius eps must be finite and > 0";
+    return RQA_EINVAL;
+  }
+  if (st->norm < 0 || st->norm > 2) {
+    *msg = "norm must be RQA_NORM_MAX, RQA_NORM_L2 or RQA_NORM_L1";
+    return RQA_EINVAL;
+  }
+  if (st->theiler < 0) {
+    *msg = "Theiler window must be >= 0";
+    return RQA_EINVAL;
+  }
+  if (st->l_min < 1 || st->v_min < 1 || st->w_min < 1) {
+    *msg = "minimum line lengths must be >= 1";
+    return RQA_EINVAL;
+  }
+  if (st->precision < 0 || st->precision > 2) {
+    *msg = "precision must be RQA_PREC_AUTO, RQA_PREC_FP32_RECHECK or RQA_PREC_FP64";
+    return RQA_EINVAL;
+  }
+  if (std::isnan(st->band_override)) {
+    *msg = "band_override is NaN";
+    return RQA_EINVAL;
+  }
+  return RQA_OK;
+}
+
+TileConfig choose_tile(int64_t n, int m, int norm) {
+  (void)m;
+  (void)norm;
+  TileConfig c{1, 4};
+  if (n >= 65536)
+    c.warps = 8;
+  else if (n >= 16384)
+    c.warps = 4;
+  else if (n >= 4096)
+    c.warps = 2;
+  if (const char* e = std::getenv("RQA_TILE_WARPS")) {
+    const int w = std::atoi(e);
+    if (w >= 1 && w <= 8) c.warps = w;
+  }
+  return c;
+}
+
+size_t series_device_bytes(const rqa_settings& st, int64_t N) {
+  const Sizes z = sizes_for(st, N, true);
+  return z.hist + z.ends + z.cnt + z.desc + z.series + z.xe + align256(sizeof(SeriesDesc)) +
+         align256(sizeof(Item) * static_cast<size_t>(z.nstrips)) + 256;
+}
+
+Engine::Engine(int device) : dev_(device) {
+  cudaSetDevice(dev_);
+  cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev_);
+  cudaStreamCreateWithFlags(&own_, cudaStreamNonBlocking);
+  for (auto& e : ev_) cudaEventCreate(&e);
+}
+
+Engine::~Engine() {
+  cudaSetDevice(dev_);
+  if (graph_) cudaGraphExecDestroy(graph_);
+  for (auto& e : ev_)
+    if (e) cudaEventDestroy(e);
+  if (own_) cudaStreamDestroy(own_);
+  if (arena_) cudaFree(arena_);
+  if (host_) cudaFreeHost(host_);
+}
+
+int Engine::fail(int code, const std::string& msg) {
+  err_ = msg;
+  return code;
+}
+
+int Engine::cuda_fail(cudaError_t e, const char* what) {
+  err_ = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return e == cudaErrorMemoryAllocation ? RQA_ENOMEM : RQA_ECUDA;
+}
+
+int Engine::ensure_arena(size_t bytes) {
+  if (bytes <= arena_cap_) return RQA_OK;
+  if (graph_) {
+    cudaGraphExecDestroy(graph_);
+    graph_ = nullptr;
+    graph_key_.clear();
+  }
+  if (arena_) {
+    cudaFree(arena_);
+    arena_ = nullptr;
+    arena_cap_ = 0;
+  }
+  const size_t cap = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&arena_, cap);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    arena_ = nullptr;
+    return cuda_fail(e, "cudaMalloc(device arena)");
+  }
+  arena_cap_ = cap;
+  return RQA_OK;
+}
+
+int Engine::ensure_host(size_t bytes) {
+  if (bytes <= host_cap_) return RQA_OK;
+  if (graph_) {
+    cudaGraphExecDestroy(graph_);
+    graph_ = nullptr;
+    graph_key_.clear();
+  }
+  if (host_) {
+    cudaFreeHost(host_);
+    host_ = nullptr;
+    host_cap_ = 0;
+  }
+  const size_t cap = bytes + bytes / 8;
+  cudaError_t e = cudaMallocHost(&host_, cap);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    host_ = nullptr;
+    return cuda_fail(e, "cudaMallocHost(staging)");
+  }
+  host_cap_ = cap;
+  return RQA_OK;
+}
+
+int Engine::run(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& results,
+                cudaStream_t stream, bool use_graph) {
+  const int rc = run_impl(in, results, stream, use_graph);
+  if (rc != RQA_OK)  // a failure of the whole set marks every unfinished series
+    for (auto& r : results)
+      if (r.status == RQA_OK && r.hist.empty()) r.status = rc;
+  return rc;
+}
+
+int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& results,
+                     cudaStream_t stream, bool use_graph) {
+  err_.clear();
+  cudaError_t ce = cudaSetDevice(dev_);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
+  const int count = static_cast<int>(in.size());
+  results.assign(count, SeriesResult{});
+  if (count == 0) return RQA_OK;
+  cudaStream_t st = stream ? stream : own_;
+
+  // ---- plan: validation, sizes, kernel classes
+  struct P {
+    Sizes z;
+    int cls = -1;
+    bool run = false;
+    size_t o_hist, o_ends, o_cnt, o_desc, o_series, o_xe;
+  };
+  std::vector<P> plan(count);
+  using Key = std::tuple<int, int, int, int>;  // m, norm, f64, warps
+  std::map<Key, int> cls_of;
+  std::vector<Key> classes;
+  int64_t max_n = 0, max_n_mp = 0, total_items = 0;
+  bool any_fp32 = false;
+  for (int q = 0; q < count; ++q) {
+    std::string msg;
+    int s = validate_settings(&in[q].st, &msg);
+    if (s == RQA_OK && !in[q].host && !in[q].dev) {
+      s = RQA_EINVAL;
+      msg = "series pointer is NULL";
+    }
+    if (s == RQA_OK && in[q].N < 1) {
+      s = RQA_ESHORT;
+      msg = "series is empty";
+    }
+    if (s == RQA_OK && nvec_of(in[q].st, in[q].N) < 1) {
+      s = RQA_ESHORT;
+      msg = "series shorter than the embedding window (m-1)*tau + 1";
+    }
+    if (s == RQA_OK && nvec_of(in[q].st, in[q].N) > RQA_MAX_N) {
+      s = RQA_ETOOBIG;
+      msg = "more than RQA_MAX_N embedded vectors";
+    }
+    if (s != RQA_OK) {
+      results[q].status = s;
+      if (count == 1) return fail(s, msg);
+      continue;
+    }
+    P& p = plan[q];
+    p.z = sizes_for(in[q].st, in[q].N, in[q].dev == nullptr);
+    p.run = true;
+    const Key k{in[q].st.m, in[q].st.norm, p.z.f64 ? 1 : 0, p.z.tc.warps};
+    auto it = cls_of.find(k);
+    if (it == cls_of.end()) {
+      it = cls_of.emplace(k, static_cast<int>(classes.size())).first;
+      classes.push_back(k);
+    }
+    p.cls = it->second;
+    max_n = std::max(max_n, p.z.n);
+    if (!p.z.f64) {
+      any_fp32 = true;
+      max_n_mp = std::max(max_n_mp, p.z.n * p.z.mp);
+    }
+    total_items += p.z.nstrips;
+  }
+  const int ncls = static_cast<int>(classes.size());
+  if (ncls == 0) return RQA_OK;
+
+  // ---- arena layout: [descs][items][queues | hists | counters | ends | boundary
+  // descriptors (zeroed)][series copies | FP32 vectors]
+  size_t off = 0;
+  const size_t o_sd = off;
+  off += align256(sizeof(SeriesDesc) * count);
+  const size_t o_items = off;
+  off += align256(sizeof(Item) * static_cast<size_t>(std::max<int64_t>(total_items, 1)));
+  const size_t o_zero = off;
+  const size_t o_queue = off;
+  off += align256(sizeof(int) * ncls);
+  const size_t o_hist0 = off;
+  for (auto& p : plan)
+    if (p.run) {
+      p.o_hist = off;
+      off += p.z.hist;
+    }
+  const size_t hist_bytes = off - o_hist0;
+  const size_t o_cnt0 = off;
+  for (auto& p : plan)
+    if (p.run) {
+      p.o_cnt = off;
+      off += p.z.cnt;
+    }
+  const size_t cnt_bytes = off - o_cnt0;
+  for (auto& p : plan)
+    if (p.run) {
+      p.o_ends = off;
+      off += p.z.ends;
+      p.o_desc = off;
+      off += p.z.desc;
+    }
+  const size_t zero_bytes = off - o_zero;
+  const size_t o_series0 = off;
+  for (auto& p : plan)
+    if (p.run) {
+      p.o_series = off;
+      off += p.z.series;
+    }
+  const size_t series_bytes = off - o_series0;
+  for (auto& p : plan)
+    if (p.run) {
+      p.o_xe = off;
+      off += p.z.xe;
+    }
+  const size_t arena_bytes = off;
+
+  // host staging: [descs][items][hist readback][counter readback][series]
+  size_t hoff = 0;
+  const size_t h_sd = hoff;
+  hoff += align256(sizeof(SeriesDesc) * count);
+  const size_t h_items = hoff;
+  hoff += align256(sizeof(Item) * static_cast<size_t>(std::max<int64_t>(total_items, 1)));
+  const size_t h_hist = hoff;
+  hoff += hist_bytes;
+  const size_t h_cnt = hoff;
+  hoff += cnt_bytes;
+  const size_t h_series = hoff;
+  hoff += series_bytes;
+
+  int rc = ensure_arena(arena_bytes);
+  if (rc != RQA_OK) return rc;
+  rc = ensure_host(hoff);
+  if (rc != RQA_OK) return rc;
+
+  // ---- fill staging
+  SeriesDesc* hsd = reinterpret_cast<SeriesDesc*>(host_ + h_sd);
+  std::memset(hsd, 0, sizeof(SeriesDesc) * count);
+  for (int q = 0; q < count; ++q) {
+    const P& p = plan[q];
+    if (!p.run) continue;
+    const rqa_settings& s = in[q].st;
+    SeriesDesc& d = hsd[q];
+    if (in[q].dev) {
+      d.s = in[q].dev;
+    } else {
+      d.s = reinterpret_cast<const double*>(arena_ + p.o_series);
+      std::memcpy(host_ + h_series + (p.o_series - o_series0), in[q].host,
+                  sizeof(double) * static_cast<size_t>(in[q].N));
+    }
+    d.xe = p.z.f64 ? nullptr : reinterpret_cast<float*>(arena_ + p.o_xe);
+    d.N = in[q].N;
+    d.n = p.z.n;
+    d.m = s.m;
+    d.tau = s.tau;
+    d.norm = s.norm;
+    d.w = s.theiler;
+    d.mp = p.z.mp;
+    d.sw = 32 * p.z.tc.warps * p.z.tc.cols;
+    d.eps = s.eps;
+    d.band_override = s.band_override;
+    d.hist = reinterpret_cast<unsigned long long*>(arena_ + p.o_hist);
+    const size_t dbytes = p.z.desc / 4;
+    d.row_a = reinterpret_cast<uint16_t*>(arena_ + p.o_desc);
+    d.row_z = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + dbytes);
+    d.dia_a = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + 2 * dbytes);
+    d.dia_z = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + 3 * dbytes);
+    d.colend = reinterpret_cast<uint32_t*>(arena_ + p.o_ends);
+    d.rowend = d.colend + p.z.n;
+    d.counters = reinterpret_cast<unsigned long long*>(arena_ + p.o_cnt);
+  }
+  // work items per class, longest strips first
+  Item* hitems = reinterpret_cast<Item*>(host_ + h_items);
+  std::vector<int64_t> cls_start(ncls + 1, 0);
+  {
+    std::vector<std::vector<std::pair<int64_t, Item>>> per(ncls);
+    for (int q = 0; q < count; ++q) {
+      const P& p = plan[q];
+      if (!p.run) continue;
+      const int64_t sw = 32LL * p.z.tc.warps * p.z.tc.cols;
+      for (int64_t Q = 0; Q < p.z.nstrips; ++Q)
+        per[p.cls].push_back({p.z.n - Q * sw, Item{q, static_cast<int32_t>(Q)}});
+    }
+    int64_t pos = 0;
+    for (int c = 0; c < ncls; ++c) {
+      std::stable_sort(per[c].begin(), per[c].end(),
+                       [](const auto& a, const auto& b) { return a.first > b.first; });
+      cls_start[c] = pos;
+      for (auto& e : per[c]) hitems[pos++] = e.second;
+    }
+    cls_start[ncls] = pos;
+  }
+
+  // ---- launch sequence
+  SeriesDesc* d_sd = reinterpret_cast<SeriesDesc*>(arena_ + o_sd);
+  Item* d_items = reinterpret_cast<Item*>(arena_ + o_items);
+  int* d_queue = reinterpret_cast<int*>(arena_ + o_queue);
+
+  std::vector<int64_t> key;
+  if (use_graph) {
+    key.push_back(count);
+    key.push_back(reinterpret_cast<int64_t>(arena_));
+    key.push_back(reinterpret_cast<int64_t>(host_));
+    key.push_back(reinterpret_cast<int64_t>(st));
+    for (int q = 0; q < count; ++q) {
+      key.push_back(in[q].N);
+      key.push_back(plan[q].run ? 1 : 0);
+      key.push_back(reinterpret_cast<int64_t>(in[q].dev));
+      key.push_back(in[q].st.m);
+      key.push_back(in[q].st.norm);
+      key.push_back(in[q].st.precision);
+      key.push_back(in[q].st.tau);
+    }
+  }
+  const bool replay = use_graph && graph_ && key == graph_key_;
+
+  auto enqueue = [&]() -> int {
+    cudaError_t e;
+    if ((e = cudaEventRecord(ev_[0], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaMemsetAsync(arena_ + o_zero, 0, zero_bytes, st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemsetAsync");
+    if ((e = cudaMemcpyAsync(arena_ + o_sd, host_ + h_sd, (o_zero - o_sd), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync(descriptors)");
+    if (series_bytes &&
+        (e = cudaMemcpyAsync(arena_ + o_series0, host_ + h_series, series_bytes,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync(series)");
+    launch_prepare(d_sd, count, st);
+    if (any_fp32) launch_embed(d_sd, count, max_n_mp, sms_, st);
+    if ((e = cudaEventRecord(ev_[1], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    for (int c = 0; c < ncls; ++c) {
+      const int m = std::get<0>(classes[c]), norm = std::get<1>(classes[c]);
+      const bool f64 = std::get<2>(classes[c]) != 0;
+      const int warps = std::get<3>(classes[c]);
+      TileFn fn = tile_kernel_for(m, norm, 4, f64);
+      if (!fn) return fail(RQA_EINVAL, "no tile kernel for this (m, norm)");
+      const size_t smem = tile_smem_for(m, f64, warps);
+      if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem))) != cudaSuccess)
+        return cuda_fail(e, "cudaFuncSetAttribute");
+      int per_sm = 0;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+               &per_sm, reinterpret_cast<const void*>(fn), 32 * warps, smem)) != cudaSuccess)
+        return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+      const int64_t nit = cls_start[c + 1] - cls_start[c];
+      const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nit, (int64_t)per_sm * sms_));
+      const SeriesDesc* a_sd = d_sd;
+      const Item* a_items = d_items + cls_start[c];
+      int a_n = static_cast<int>(nit);
+      int* a_queue = d_queue + c;
+      void* args[] = {&a_sd, &a_items, &a_n, &a_queue};
+      if ((e = cudaLaunchKernel(reinterpret_cast<const void*>(fn),
+                                dim3(static_cast<unsigned>(grid)), dim3(32 * warps), args, smem,
+                                st)) != cudaSuccess)
+        return cuda_fail(e, "tile kernel launch");
+    }
+    if ((e = cudaEventRecord(ev_[2], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    launch_merges(d_sd, count, max_n, sms_, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "merge kernels launch");
+    if ((e = cudaMemcpyAsync(host_ + h_hist, arena_ + o_hist0, hist_bytes + cnt_bytes,
+                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync(histograms)");
+    if ((e = cudaMemcpyAsync(host_ + h_sd, arena_ + o_sd, sizeof(SeriesDesc) * count,
+                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync(series state)");
+    if ((e = cudaEventRecord(ev_[3], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    return RQA_OK;
+  };
+
+  if (use_graph) {
+    if (!replay) {
+      if (graph_) {
+        cudaGraphExecDestroy(graph_);
+        graph_ = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+      rc = enqueue();
+      e = cudaStreamEndCapture(st, &g);
+      if (rc != RQA_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&graph_, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        graph_ = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+      }
+      graph_key_ = key;
+    }
+    cudaError_t e = cudaGraphLaunch(graph_, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  } else {
+    rc = enqueue();
+    if (rc != RQA_OK) return rc;
+  }
+  ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
+  cudaEventElapsedTime(&tile_ms_, ev_[1], ev_[2]);
+  cudaEventElapsedTime(&total_ms_, ev_[0], ev_[3]);
+  last_sd_ = d_sd;
+  last_f64_ = plan[0].run && plan[0].z.f64;
+  last_stream_ = st;
+
+  // ---- results
+  int first_err = RQA_OK;
+  for (int q = 0; q < count; ++q) {
+    const P& p = plan[q];
+    SeriesResult& r = results[q];
+    if (!p.run) {
+      if (first_err == RQA_OK) first_err = r.status;
+      continue;
+    }
+    const uint64_t* cnt = reinterpret_cast<const uint64_t*>(host_ + h_cnt + (p.o_cnt - o_cnt0));
+    const SeriesDesc& d = hsd[q];
+    r.n = p.z.n;
+    r.status = static_cast<int>(cnt[CNT_STATUS]);
+    if (r.status == RQA_OK) {
+      const uint64_t* h = reinterpret_cast<const uint64_t*>(host_ + h_hist + (p.o_hist - o_hist0));
+      r.hist.assign(h, h + 3 * (p.z.n + 1));
+      measures_from_histograms(r.hist.data(), r.hist.data() + (p.z.n + 1),
+                               r.hist.data() + 2 * (p.z.n + 1), p.z.n, in[q].st.l_min,
+                               in[q].st.v_min, in[q].st.w_min, &r.meas);
+    } else if (first_err == RQA_OK) {
+      first_err = r.status;
+      err_ = r.status == RQA_ENAN       ? "series contains NaN or infinite values"
+             : r.status == RQA_ETIMEOUT ? "a bounded device-side wait gave up"
+                                        : "internal error: a line length outside 1..n";
+    }
+    rqa_stats_t& s = r.stats;
+    s.n_vec = p.z.n;
+    s.pairs = pair_count(p.z.n, in[q].st.theiler);
+    s.rechecks = static_cast<int64_t>(cnt[CNT_RECHECKS]);
+    s.precision_used = p.z.f64 ? RQA_PREC_FP64 : RQA_PREC_FP32_RECHECK;
+    s.band = p.z.f64 ? 0.0 : d.band_rel;
+    s.band_bound = p.z.f64 ? 0.0 : d.bound_rel;
+    s.exact = (p.z.f64 || d.band_rel >= d.bound_rel) ? 1 : 0;
+    s.strip_width = 32 * p.z.tc.warps * p.z.tc.cols;
+    s.warps_per_cta = p.z.tc.warps;
+    s.cols_per_lane = p.z.tc.cols;
+    s.kernel_ms = tile_ms_;
+    s.total_ms = total_ms_;
+  }
+  return first_err;
+}
+
+int Engine::sample(const int64_t* i, const int64_t* j, int64_t count, uint8_t* out) {
+  if (!last_sd_) return fail(RQA_EINVAL, "no run to sample from");
+  if (count <= 0) return RQA_OK;
+  cudaError_t e = cudaSetDevice(dev_);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  void* buf = nullptr;
+  const size_t bytes = count * (2 * sizeof(int64_t) + 1);
+  if ((e = cudaMalloc(&buf, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sample)");
+  int64_t* di = static_cast<int64_t*>(buf);
+  int64_t* dj = di + count;
+  uint8_t* dout = reinterpret_cast<uint8_t*>(dj + count);
+  cudaStream_t st = own_;
+  int rc = RQA_OK;
+  if ((e = cudaMemcpyAsync(di, i, count * sizeof(int64_t), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(dj, j, count * sizeof(int64_t), cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+    rc = cuda_fail(e, "cudaMemcpyAsync(sample)");
+  } else {
+    launch_sample(last_sd_, di, dj, count, dout, last_f64_ ? 1 : 0, st);
+    if ((e = cudaMemcpyAsync(out, dout, count, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      rc = cuda_fail(e, "sample kernel");
+  }
+  cudaFree(buf);
+  return rc;
+}
+
+}  // namespace rqa

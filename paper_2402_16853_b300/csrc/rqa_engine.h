@@ -1,0 +1,95 @@
+// rqa_engine.h -- run engine shared by the single-series, batched and served
+// entry points: plans device memory for a set of series, launches prepare ->
+// embed -> tile (one persistent launch per kernel class) -> merge ->
+// finalize on one stream, and turns the histograms into measures.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/rqa.h"
+#include "rqa_internal.h"
+
+namespace rqa {
+
+struct SeriesInput {
+  rqa_settings st;
+  const double* host = nullptr;  // copied to the device
+  const double* dev = nullptr;   // used in place (caller's device memory)
+  int64_t N = 0;
+};
+
+struct SeriesResult {
+  int status = RQA_OK;
+  int64_t n = 0;
+  std::vector<uint64_t> hist;  // 3 * (n + 1): diagonal, vertical, white vertical
+  rqa_measures_t meas{};
+  rqa_stats_t stats{};
+};
+
+// Validation shared by every entry point.  Returns RQA_OK or an error code
+// and a message.
+int validate_settings(const rqa_settings* st, std::string* msg);
+
+// Tile configuration for a series of n vectors (warps per CTA strip,
+// columns per lane); may be overridden by RQA_TILE_WARPS for tuning.
+TileConfig choose_tile(int64_t n, int m, int norm);
+
+// Device bytes a series of length N needs (for admission control).
+size_t series_device_bytes(const rqa_settings& st, int64_t N);
+
+void measures_from_histograms(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
+                              int64_t n, int32_t l_min, int32_t v_min, int32_t w_min,
+                              rqa_measures_t* out);
+
+class Engine {
+ public:
+  explicit Engine(int device);
+  ~Engine();
+  Engine(const Engine&) = delete;
+  Engine& operator=(const Engine&) = delete;
+
+  // Run a set of series on `stream` (nullptr: the engine's own stream).
+  // Returns RQA_OK if the set ran (per-series failures are in
+  // results[q].status), or an error that affected the whole set.
+  int run(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& results,
+          cudaStream_t stream, bool use_graph);
+
+  // Decisions R_ij of series 0 of the last run (needs its buffers alive).
+  int sample(const int64_t* i, const int64_t* j, int64_t count, uint8_t* out);
+
+  const std::string& error() const { return err_; }
+  int device() const { return dev_; }
+  int sm_count() const { return sms_; }
+  float last_tile_ms() const { return tile_ms_; }
+  float last_total_ms() const { return total_ms_; }
+
+ private:
+  int run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& results,
+               cudaStream_t stream, bool use_graph);
+  int ensure_arena(size_t bytes);
+  int ensure_host(size_t bytes);
+  int fail(int code, const std::string& msg);
+  int cuda_fail(cudaError_t e, const char* what);
+
+  int dev_ = 0, sms_ = 0;
+  cudaStream_t own_ = nullptr;
+  unsigned char* arena_ = nullptr;
+  size_t arena_cap_ = 0;
+  unsigned char* host_ = nullptr;  // pinned staging
+  size_t host_cap_ = 0;
+  cudaEvent_t ev_[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::string err_;
+  float tile_ms_ = 0.f, total_ms_ = 0.f;
+  // last run, for sample()
+  SeriesDesc* last_sd_ = nullptr;
+  bool last_f64_ = false;
+  cudaStream_t last_stream_ = nullptr;
+  // graph cache (batched runs with an unchanged plan)
+  cudaGraphExec_t graph_ = nullptr;
+  std::vector<int64_t> graph_key_;
+};
+
+}  // namespace rqa

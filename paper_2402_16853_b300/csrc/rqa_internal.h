@@ -1,0 +1,60 @@
+// rqa_internal.h -- structures shared by the host side and the CUDA kernels of
+// librqa_b300.so.  Nothing here is part of the public C ABI (include/rqa.h).
+#pragma once
+#include <stdint.h>
+
+namespace rqa {
+
+// Per-series state in device memory.  The host fills the inputs and buffer
+// pointers; the prepare kernel fills the FP32 constants.
+struct SeriesDesc {
+  // ---- inputs
+  const double* s;      // FP64 series, N values (device)
+  float* xe;            // embedded FP32 vectors, [n][mp] (device)
+  int64_t N;            // series length
+  int64_t n;            // embedded vectors, N - (m-1) tau
+  int32_t m, tau, norm, w;
+  int32_t mp;           // floats per stored vector (m rounded up to 4)
+  int32_t sw;           // columns per CTA strip
+  double eps;
+  double band_override; // < 0: automatic
+  // ---- filled by the prepare kernel
+  double center, scale; // x32 = fl32((s - center) * scale)
+  float thr;            // FP32 threshold: eps*scale (L1, max) or its square (L2)
+  float band;           // |acc| <= band -> re-decide in FP64
+  double band_rel;      // band / eps (eps^2 for L2)
+  double bound_rel;     // proven sufficient band, same units
+  // ---- outputs (device)
+  unsigned long long* hist;   // [3][n+1]: upper diagonals, vertical, white vertical
+  uint16_t* row_a;            // boundary descriptors, strip-triangular layout
+  uint16_t* row_z;
+  uint16_t* dia_a;
+  uint16_t* dia_z;
+  uint32_t* colend;           // [n] run of column j touching row j-1
+  uint32_t* rowend;           // [n] run of row i touching column i+1
+  unsigned long long* counters;  // [0] rechecks, [1] status (rqa_status)
+};
+
+enum { HIST_DIAG = 0, HIST_VERT = 1, HIST_WHITE = 2 };
+enum { CNT_RECHECKS = 0, CNT_STATUS = 1, CNT_WORDS = 2 };
+
+// Offset of strip Q's descriptors: strips hold J1(Q) - 1 entries each, with
+// J1(Q) = n - Q*sw the exclusive right end of the strip.
+__host__ __device__ inline int64_t strip_offset(int64_t n, int64_t sw, int64_t Q) {
+  return Q * (n - 1) - sw * (Q * (Q - 1) / 2);
+}
+__host__ __device__ inline int64_t num_strips(int64_t n, int64_t sw) {
+  return n >= 2 ? (n - 2) / sw + 1 : 0;
+}
+
+struct Item {
+  int32_t series;
+  int32_t strip;
+};
+
+struct TileConfig {
+  int warps;   // warps per CTA (warps of one CTA strip, right to left)
+  int cols;    // columns per lane (C): a warp covers 32*C columns
+};
+
+}  // namespace rqa

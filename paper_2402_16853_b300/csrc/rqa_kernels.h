@@ -1,0 +1,28 @@
+// rqa_kernels.h -- host-side entry points of the CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "rqa_internal.h"
+
+namespace rqa {
+
+using TileFn = void (*)(const SeriesDesc*, const Item*, int, int*);
+
+// Fused tile kernel for embedding dimension m (1..10), norm (0 max, 1 L2,
+// 2 L1), columns per lane `cols` (4) and FP64-everywhere or FP32 + recheck.
+TileFn tile_kernel_for(int m, int norm, int cols, bool f64);
+size_t tile_smem_for(int m, bool f64, int warps);
+
+TileFn tile_kernel_norm0(int m, int cols, bool f64);
+TileFn tile_kernel_norm1(int m, int cols, bool f64);
+TileFn tile_kernel_norm2(int m, int cols, bool f64);
+
+void launch_prepare(SeriesDesc* d_sd, int count, cudaStream_t st);
+void launch_embed(SeriesDesc* d_sd, int count, int64_t max_n_mp, int sms, cudaStream_t st);
+void launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, int sms, cudaStream_t st);
+void launch_sample(const SeriesDesc* d_sd, const int64_t* ii, const int64_t* jj, int64_t count,
+                   uint8_t* out, int f64, cudaStream_t st);
+
+}  // namespace rqa

@@ -1,0 +1,21 @@
+// tile_dispatch.cu -- selects the tile kernel instantiation for a series.
+#include "rqa_kernels.h"
+#include "rqa_tile.cuh"
+
+namespace rqa {
+
+TileFn tile_kernel_for(int m, int norm, int cols, bool f64) {
+  switch (norm) {
+    case 0: return tile_kernel_norm0(m, cols, f64);
+    case 1: return tile_kernel_norm1(m, cols, f64);
+    case 2: return tile_kernel_norm2(m, cols, f64);
+    default: return nullptr;
+  }
+}
+
+size_t tile_smem_for(int m, bool f64, int warps) {
+  const int row_elems = f64 ? m : ((m + 3) / 4) * 4;
+  return tile_smem_bytes(warps, row_elems, f64 ? 8 : 4);
+}
+
+}  // namespace rqa

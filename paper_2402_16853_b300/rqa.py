@@ -1,0 +1,349 @@
+"""ctypes binding of librqa_b300.so (include/rqa.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  There is no CPU fallback: if the native library is
+missing this module raises at load time, and on a machine without a B300 the
+library's own calls return RQA_ENODEV.
+
+PyTorch is used only to hand device memory and streams to the library
+(``RQA.run`` with a CUDA tensor passes its data pointer and the current
+stream to ``rqa_run_device``).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librqa_b300.so")
+
+RQA_OK, RQA_EINVAL, RQA_ESHORT, RQA_ENAN, RQA_ENOMEM, RQA_ECUDA = 0, 1, 2, 3, 4, 5
+RQA_ETIMEOUT, RQA_PENDING, RQA_ENODEV, RQA_ETOOBIG, RQA_ENOTFOUND = 6, 7, 8, 9, 10
+NORM_MAX, NORM_L2, NORM_L1 = 0, 1, 2
+PREC_AUTO, PREC_FP32_RECHECK, PREC_FP64 = 0, 1, 2
+HIST_DIAGONAL, HIST_VERTICAL, HIST_WHITE = 0, 1, 2
+
+
+class RQAError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {strerror(status)} ({status})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+@dataclass(frozen=True)
+class Settings:
+    """The paper's Settings (Sect. 7.2): embedding, norm, radius, Theiler
+    window and minimum line lengths, plus the GPU precision mode."""
+    m: int
+    tau: int
+    eps: float
+    norm: int = NORM_L2
+    theiler: int = 1
+    l_min: int = 2
+    v_min: int = 2
+    w_min: int = 2
+    precision: int = PREC_AUTO
+    band_override: float = -1.0
+
+
+class _CSettings(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("tau", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("norm", ctypes.c_int32), ("theiler", ctypes.c_int32),
+                ("l_min", ctypes.c_int32), ("v_min", ctypes.c_int32),
+                ("w_min", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("band_override", ctypes.c_double)]
+
+
+_MEAS_D = ("rr", "det", "l", "div", "l_entr", "lam", "tt", "v_entr", "w", "w_entr")
+_MEAS_I = ("l_max", "v_max", "w_max", "n_vec", "recurrence_points")
+
+
+class _CMeasures(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in _MEAS_D] + [(k, ctypes.c_int64) for k in _MEAS_I]
+
+
+class _CStats(ctypes.Structure):
+    _fields_ = [("n_vec", ctypes.c_int64), ("pairs", ctypes.c_int64),
+                ("rechecks", ctypes.c_int64), ("band", ctypes.c_double),
+                ("band_bound", ctypes.c_double), ("precision_used", ctypes.c_int32),
+                ("exact", ctypes.c_int32), ("strip_width", ctypes.c_int32),
+                ("warps_per_cta", ctypes.c_int32), ("cols_per_lane", ctypes.c_int32),
+                ("ctas", ctypes.c_int32), ("kernel_ms", ctypes.c_float),
+                ("total_ms", ctypes.c_float)]
+
+
+MEASURE_FIELDS = list(_MEAS_D + _MEAS_I)
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the native library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with "
+                          "`python -m paper_2402_16853_b300.build`")
+    lib = ctypes.CDLL(path)
+    P, c = ctypes.POINTER, ctypes
+    vp = c.c_void_p
+    sig = {
+        "rqa_create": (c.c_int, [P(_CSettings), P(vp)]),
+        "rqa_run": (c.c_int, [vp, P(c.c_double), c.c_int64]),
+        "rqa_run_device": (c.c_int, [vp, vp, c.c_int64, vp]),
+        "rqa_measures": (c.c_int, [vp, P(_CMeasures)]),
+        "rqa_histogram": (c.c_int, [vp, c.c_int32, P(c.c_uint64), c.c_int64, P(c.c_int64)]),
+        "rqa_stats": (c.c_int, [vp, P(_CStats)]),
+        "rqa_sample_decisions": (c.c_int, [vp, P(c.c_int64), P(c.c_int64), c.c_int64,
+                                           P(c.c_uint8)]),
+        "rqa_destroy": (None, [vp]),
+        "rqa_strerror": (c.c_char_p, [c.c_int]),
+        "rqa_last_error": (c.c_char_p, [vp]),
+        "rqa_batch_create": (c.c_int, [P(vp)]),
+        "rqa_batch_run": (c.c_int, [vp, P(_CSettings), P(P(c.c_double)), P(c.c_int64),
+                                    c.c_int32, P(_CMeasures), P(c.c_int32)]),
+        "rqa_batch_histogram": (c.c_int, [vp, c.c_int32, c.c_int32, P(c.c_uint64), c.c_int64,
+                                          P(c.c_int64)]),
+        "rqa_batch_stats": (c.c_int, [vp, P(_CStats)]),
+        "rqa_batch_destroy": (None, [vp]),
+        "rqa_server_create": (c.c_int, [c.c_size_t, c.c_int32, P(vp)]),
+        "rqa_submit": (c.c_int, [vp, P(_CSettings), P(c.c_double), c.c_int64, P(c.c_uint64)]),
+        "rqa_poll": (c.c_int, [vp, c.c_uint64, P(_CMeasures)]),
+        "rqa_wait": (c.c_int, [vp, c.c_uint64, c.c_int64, P(_CMeasures)]),
+        "rqa_release": (c.c_int, [vp, c.c_uint64]),
+        "rqa_server_counters": (c.c_int, [vp] + [P(c.c_int64)] * 6),
+        "rqa_server_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(status: int) -> str:
+    return load().rqa_strerror(int(status)).decode()
+
+
+def _cs(st: Settings) -> _CSettings:
+    return _CSettings(int(st.m), int(st.tau), float(st.eps), int(st.norm), int(st.theiler),
+                      int(st.l_min), int(st.v_min), int(st.w_min), int(st.precision),
+                      float(st.band_override))
+
+
+def _meas(m: _CMeasures) -> dict:
+    return {k: getattr(m, k) for k in MEASURE_FIELDS}
+
+
+def _f64(series) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(series, dtype=np.float64))
+
+
+class RQA:
+    """One RQA computation (the paper's RQAComputation, Sect. 7.3)."""
+
+    def __init__(self, settings: Settings):
+        lib = load()
+        self.settings = settings
+        self._cs = _cs(settings)
+        h = ctypes.c_void_p()
+        rc = lib.rqa_create(ctypes.byref(self._cs), ctypes.byref(h))
+        if rc:
+            raise RQAError(rc, "rqa_create")
+        self._h = h
+        self.n = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rqa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc, where):
+        if rc:
+            raise RQAError(rc, where, load().rqa_last_error(self._h).decode())
+
+    def run(self, series, stream=None) -> dict:
+        """Run on a series: a host array (copied) or a CUDA torch tensor
+        (used in place, ordered on `stream` or torch's current stream).
+        Returns the measures."""
+        lib = load()
+        if hasattr(series, "is_cuda") and series.is_cuda:
+            import torch
+            t = series.contiguous()
+            if t.dtype != torch.float64:
+                raise TypeError("device series must be float64")
+            if stream is None:
+                stream = torch.cuda.current_stream(t.device)
+            sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+            rc = lib.rqa_run_device(self._h, ctypes.c_void_p(t.data_ptr()), t.numel(),
+                                    ctypes.c_void_p(sp))
+            n_in = t.numel()
+            self._keep = t  # the library samples from it later
+        else:
+            s = _f64(series)
+            rc = lib.rqa_run(self._h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(s))
+            n_in = len(s)
+        self._check(rc, "rqa_run")
+        self.n = n_in - (self.settings.m - 1) * self.settings.tau
+        return self.measures()
+
+    def measures(self) -> dict:
+        m = _CMeasures()
+        self._check(load().rqa_measures(self._h, ctypes.byref(m)), "rqa_measures")
+        return _meas(m)
+
+    def histogram(self, kind: int) -> np.ndarray:
+        ln = ctypes.c_int64()
+        load().rqa_histogram(self._h, kind, None, 0, ctypes.byref(ln))
+        out = np.zeros(ln.value, dtype=np.uint64)
+        self._check(load().rqa_histogram(self._h, kind,
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                         len(out), ctypes.byref(ln)), "rqa_histogram")
+        return out
+
+    def histograms(self):
+        return tuple(self.histogram(k) for k in (HIST_DIAGONAL, HIST_VERTICAL, HIST_WHITE))
+
+    def stats(self) -> dict:
+        s = _CStats()
+        self._check(load().rqa_stats(self._h, ctypes.byref(s)), "rqa_stats")
+        return {k: getattr(s, k) for k, _ in _CStats._fields_}
+
+    def sample(self, i, j) -> np.ndarray:
+        i = np.ascontiguousarray(i, dtype=np.int64)
+        j = np.ascontiguousarray(j, dtype=np.int64)
+        out = np.zeros(len(i), dtype=np.uint8)
+        P = ctypes.POINTER
+        self._check(load().rqa_sample_decisions(
+            self._h, i.ctypes.data_as(P(ctypes.c_int64)), j.ctypes.data_as(P(ctypes.c_int64)),
+            len(i), out.ctypes.data_as(P(ctypes.c_uint8))), "rqa_sample_decisions")
+        return out
+
+
+class Batch:
+    """Many series in one submission (one persistent launch per (m, norm)
+    class, captured in a CUDA graph and replayed for unchanged shapes)."""
+
+    def __init__(self):
+        lib = load()
+        h = ctypes.c_void_p()
+        rc = lib.rqa_batch_create(ctypes.byref(h))
+        if rc:
+            raise RQAError(rc, "rqa_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rqa_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, settings: Sequence[Settings], series: Sequence[np.ndarray]):
+        """Returns (list of measure dicts or None, list of statuses, rc)."""
+        k = len(series)
+        arrs = [_f64(s) for s in series]
+        cs = (_CSettings * k)(*[_cs(s) for s in settings])
+        ptrs = (ctypes.POINTER(ctypes.c_double) * k)(
+            *[a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs])
+        lens = (ctypes.c_int64 * k)(*[len(a) for a in arrs])
+        out = (_CMeasures * k)()
+        st = (ctypes.c_int32 * k)()
+        rc = load().rqa_batch_run(self._h, cs, ptrs, lens, k, out, st)
+        self._arrs = arrs
+        res = [(_meas(out[q]) if st[q] == 0 else None) for q in range(k)]
+        return res, [int(x) for x in st], int(rc)
+
+    def histogram(self, q: int, kind: int) -> np.ndarray:
+        ln = ctypes.c_int64()
+        load().rqa_batch_histogram(self._h, q, kind, None, 0, ctypes.byref(ln))
+        out = np.zeros(ln.value, dtype=np.uint64)
+        rc = load().rqa_batch_histogram(self._h, q, kind,
+                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                        len(out), ctypes.byref(ln))
+        if rc:
+            raise RQAError(rc, "rqa_batch_histogram")
+        return out
+
+    def stats(self) -> dict:
+        s = _CStats()
+        load().rqa_batch_stats(self._h, ctypes.byref(s))
+        return {k: getattr(s, k) for k, _ in _CStats._fields_}
+
+
+class Server:
+    """Continuous-batching server (rqa_server_*)."""
+
+    def __init__(self, mem_budget_bytes: int, max_slots: int = 4096):
+        lib = load()
+        h = ctypes.c_void_p()
+        rc = lib.rqa_server_create(int(mem_budget_bytes), int(max_slots), ctypes.byref(h))
+        if rc:
+            raise RQAError(rc, "rqa_server_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rqa_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, settings: Settings, series) -> int:
+        s = _f64(series)
+        cs = _cs(settings)
+        t = ctypes.c_uint64()
+        rc = load().rqa_submit(self._h, ctypes.byref(cs),
+                               s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(s),
+                               ctypes.byref(t))
+        if rc:
+            raise RQAError(rc, "rqa_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        m = _CMeasures()
+        rc = load().rqa_poll(self._h, ticket, ctypes.byref(m))
+        return rc, (_meas(m) if rc == RQA_OK else None)
+
+    def wait(self, ticket: int, timeout_ms: int = 60_000):
+        m = _CMeasures()
+        rc = load().rqa_wait(self._h, ticket, int(timeout_ms), ctypes.byref(m))
+        return rc, (_meas(m) if rc == RQA_OK else None)
+
+    def release(self, ticket: int) -> int:
+        return load().rqa_release(self._h, ticket)
+
+    def counters(self) -> dict:
+        vals = [ctypes.c_int64() for _ in range(6)]
+        load().rqa_server_counters(self._h, *[ctypes.byref(v) for v in vals])
+        keys = ("admitted", "completed", "queued", "in_flight", "bytes_in_use", "epochs")
+        return {k: v.value for k, v in zip(keys, vals)}
