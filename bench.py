@@ -1,0 +1,451 @@
+#!/usr/bin/env python
+"""Benchmark of the RQA hot path on B300.
+
+Primary line: recurrence cells/s (n^2 / step time) and the fraction of the
+FP32 ALU issue roofline of the fused tile kernel, on a 1,048,576-point AR(1)
+series (phi = 0.95, z-scored; m = 3, tau = 1, L2, eps = 0.5, Theiler 1,
+minimum line lengths 2).  A step is one complete RQA computation through the
+C ABI (embed -> fused tile kernel -> boundary merges -> line-of-identity join
+-> histograms to the host -> measures) on a series already resident in HBM;
+L2 is flushed (a 512 MiB write) before every timed step.
+
+Also reported on the same line: end-to-end cells/s through the C ABI with
+host buffers (copies inside the timed region), the FP64-everywhere GPU path
+on the same series, the batched workload (4,096 uneven series, one graph per
+call) against sequential single-series calls, the served workload (Poisson
+arrivals, p50 / p99 latency), the clocks seen during the timed region, and
+the FP64 CPU oracle timed on a bounded sample on the host's cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "ar1_n1m"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_MAX_FALLBACK = 2032.0
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--N", type=int, default=0,
+                    help="series length override (default: the 1,048,576-point workload)")
+    ap.add_argument("--cpu-stride", type=int, default=0,
+                    help="oracle sample: every k-th column and diagonal (0: pick ~15 s)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"sm_max_mhz": SM_MAX_FALLBACK}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(series, params, stride: int, target_s: float = 15.0):
+    """The FP64 oracle as it stands, on the host's cores, over every
+    stride-th column and diagonal of the same workload."""
+    import oracle
+    st = oracle.Settings(**params)
+    n = len(series) - (params["m"] - 1) * params["tau"]
+    cores = os.cpu_count() or 1
+    if stride <= 0:
+        # calibrate on a small sample, then size the run to ~target_s
+        probe = max(1, int(2 * n * n // (cores * 5e7)))   # ~0.1-1 s of work
+        t0 = time.perf_counter()
+        *_, visited = oracle.histograms_streaming(series, st, threads=cores, stride=probe)
+        dt = time.perf_counter() - t0
+        rate = visited / max(dt, 1e-6)
+        stride = max(1, int(2 * n * n / (rate * target_s)))
+    t0 = time.perf_counter()
+    *_, visited = oracle.histograms_streaming(series, st, threads=cores, stride=stride)
+    dt = time.perf_counter() - t0
+    cells_per_s = (visited / 2.0) / dt   # a cell costs one column and one diagonal visit
+    return {"value": cells_per_s, "unit": "cells/s", "cores": cores, "kind": "oracle",
+            "sample": f"every {stride}-th column and diagonal of the {n}-vector matrix "
+                      f"({visited} cell visits in {dt:.1f} s; rate = visits/2/s)",
+            "seconds": dt}
+
+
+# ------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    s, params = synth.workload(WORKLOAD)
+    n = len(s) - (params["m"] - 1) * params["tau"]
+    stride = args.cpu_stride
+    vals = []
+    cb = None
+    # W + K bounded samples, each ~5 s of CPU work
+    for k in range(max(1, args.warmup) + max(1, args.steps)):
+        cb = cpu_baseline(s, params, stride, target_s=5.0)
+        stride = int(cb["sample"].split("every ")[1].split("-th")[0])
+        if k >= max(1, args.warmup):
+            vals.append(cb["value"])
+    v = float(np.median(vals))
+    step_s = n * n / v
+    line = {"impl": "reference", "metric": "recurrence cells/s", "value": v,
+            "unit": "cells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": len(s), **params},
+            "cpu_baseline": {**cb, "value": v},
+            "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------- our arm
+def run_mine(args):
+    import torch
+    import paper_2402_16853_b300 as gp
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    peaks, peak_kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", SM_MAX_FALLBACK))
+
+    s, params = synth.workload(WORKLOAD)
+    if args.N:
+        s = synth.ar1(args.N, 1003, 0.95)
+    N = len(s)
+    n = N - (params["m"] - 1) * params["tau"]
+    st = gp.Settings(**params)
+    t_s = torch.tensor(s, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    r = gp.RQA(st)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        r.run(t_s)
+    stats0 = r.stats()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    kernel_ms = []
+    launches = 0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        flush.fill_(1)
+        r.run(t_s)
+        stt = r.stats()
+        kernel_ms.append(stt["kernel_ms"])
+        launches += stt["launches"] + 1   # + the L2 flush fill
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if dist is not None:
+        tt = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    barrier()
+    meas = r.measures()
+    stt = r.stats()
+    cells = float(n) * n
+    value = world * cells * args.steps / elapsed
+    pairs = stt["pairs"]
+    ops_per_pair = 2 * params["m"] + 1
+    k_ms = float(np.mean(kernel_ms))
+    achieved = pairs * ops_per_pair / (k_ms / 1e3) / 1e12
+    peak = sms * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("tile_kernel_dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # ---- end to end through the C ABI with host buffers
+    host = torch.tensor(s, dtype=torch.float64).pin_memory().numpy()
+    r.run(host)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        flush.fill_(1)
+        r.run(host)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    st_e2e = r.stats()
+    e2e = {"value": world * cells * e2e_steps / e2e_s, "unit": "cells/s",
+           "h2d_bytes_per_step": int(st_e2e["h2d_bytes"]),
+           "d2h_bytes_per_step": int(st_e2e["d2h_bytes"])}
+
+    extra = {}
+    # ---- FP64-everywhere GPU path on the same series
+    if not args.no_fp64:
+        r64 = gp.RQA(gp.Settings(**params, precision=gp.PREC_FP64))
+        r64.run(t_s)
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        r64.run(t_s)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        t64 = a0.elapsed_time(a1) / 1e3
+        m64 = r64.measures()
+        same = all((meas[k] == m64[k]) or (isinstance(meas[k], float) and math.isnan(meas[k])
+                                            and math.isnan(m64[k])) for k in meas)
+        extra["fp64_path"] = {"value": cells / t64, "unit": "cells/s",
+                              "kernel_ms": r64.stats()["kernel_ms"],
+                              "speedup_fp32_recheck": (cells / (elapsed / args.steps)) /
+                                                      (cells / t64),
+                              "measures_identical": bool(same)}
+        del r64
+
+    # ---- batched workload vs sequential single-series calls
+    if not args.no_batch:
+        extra["batched"] = bench_batch(gp, args, dev, barrier)
+
+    # ---- served workload
+    if not args.no_serve:
+        extra["served"] = bench_serve(gp, args)
+
+    line = {
+        "metric": "recurrence cells/s", "value": value, "unit": "cells/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "n_vec": n, **params,
+                   "series": "AR(1) phi=0.95, N(0,1) noise, z-scored, seed 1003",
+                   "l2": "flushed before every timed step (512 MiB write)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single GPU"},
+        "pairs_per_s": world * pairs * args.steps / elapsed,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "tile_kernel<3,L2,4,fp32>", "kernel_ms": k_ms,
+                     "ops_per_pair": ops_per_pair, "pairs_per_launch": pairs,
+                     "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} "
+                                   f"MHz ({peak_kind} sm_max_mhz)"},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "rechecks_per_step": int(stt["rechecks"]), "recheck_band_rel": stt["band"],
+        "exact": bool(stt["exact"]),
+        "measures": {k: meas[k] for k in ("rr", "det", "l", "l_max", "lam", "tt", "v_max")},
+        **extra,
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(s, params, args.cpu_stride)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def bench_batch(gp, args, dev, barrier):
+    import torch
+    specs = synth.batch_specs(args.batch_count)
+    series, eps = synth.make_series(specs, seed=2004)
+    settings = [gp.Settings(m=sp.m, tau=sp.tau, eps=e, norm=sp.norm, theiler=sp.theiler,
+                            l_min=sp.l_min, v_min=sp.v_min, w_min=sp.w_min)
+                for sp, e in zip(specs, eps)]
+    b = gp.Batch()
+    res, status, rc = b.run(settings, series)   # captures the graph
+    assert rc == 0, status
+    b.run(settings, series)
+    steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        res2, st2, rc2 = b.run(settings, series)
+    t_batch = (time.perf_counter() - t0) / steps
+    bst = b.stats()
+    # sequential single-series calls of the same kernels
+    t0 = time.perf_counter()
+    seq = []
+    for stg, s in zip(settings, series):
+        rr = gp.RQA(stg)
+        seq.append(rr.run(s))
+        rr.close()
+    t_seq = time.perf_counter() - t0
+    same = all(a == bb or (isinstance(a, float) and math.isnan(a) and math.isnan(bb))
+               for m1, m2 in zip(res2, seq) for a, bb in zip(m1.values(), m2.values()))
+    cells = float(sum((len(s) - (sp.m - 1) * sp.tau) ** 2 for s, sp in zip(series, specs)))
+    return {"series": len(series), "series_per_s": len(series) / t_batch,
+            "cells_per_s": cells / t_batch, "ms_per_batch": t_batch * 1e3,
+            "kernel_ms": bst["kernel_ms"], "device_ms": bst["total_ms"],
+            "sequential_series_per_s": len(series) / t_seq,
+            "speedup_vs_sequential": t_seq / t_batch, "identical_to_sequential": bool(same),
+            "graph": "captured once, replayed"}
+
+
+def bench_serve(gp, args):
+    arrivals, specs, series, eps = synth.serve_stream(duration=args.serve_seconds)
+    settings = [gp.Settings(m=sp.m, tau=sp.tau, eps=e, norm=sp.norm, theiler=sp.theiler,
+                            l_min=sp.l_min, v_min=sp.v_min, w_min=sp.w_min)
+                for sp, e in zip(specs, eps)]
+    srv = gp.Server(40 << 30, max_slots=4096)
+    # warm the engines
+    t = srv.submit(settings[0], series[0])
+    srv.wait(t)
+    srv.release(t)
+    lat = [None] * len(series)
+    done_at = [None] * len(series)
+    tickets = [None] * len(series)
+    t0 = time.perf_counter()
+    submit_at = [None] * len(series)
+
+    def poller():
+        pending = set()
+        q = 0
+        while q < len(series) or pending:
+            while q < len(series) and tickets[q] is not None:
+                pending.add(q)
+                q += 1
+            fin = []
+            for k in pending:
+                rc, _ = srv.poll(tickets[k])
+                if rc != gp.rqa.RQA_PENDING:
+                    done_at[k] = time.perf_counter()
+                    fin.append(k)
+            for k in fin:
+                pending.discard(k)
+                srv.release(tickets[k])
+            if not fin:
+                time.sleep(0.0005)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    for k, (a, stg, s) in enumerate(zip(arrivals, settings, series)):
+        now = time.perf_counter() - t0
+        if a > now:
+            time.sleep(a - now)
+        submit_at[k] = time.perf_counter()
+        tickets[k] = srv.submit(stg, s)
+    th.join()
+    t_end = max(done_at)
+    lat = np.array([d - s0 for d, s0 in zip(done_at, submit_at)])
+    cells = float(sum((len(s) - (sp.m - 1) * sp.tau) ** 2 for s, sp in zip(series, specs)))
+    ctr = srv.counters()
+    srv.close()
+    wall = t_end - t0
+    return {"requests": len(series), "offered_rate_per_s": len(series) / args.serve_seconds,
+            "series_per_s": len(series) / wall, "cells_per_s": cells / wall,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "max_ms": float(lat.max() * 1e3), "epochs": ctr["epochs"],
+            "budget_bytes": 40 << 30, "seconds_of_arrivals": args.serve_seconds}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mine(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -127,6 +127,10 @@ typedef struct {
   int32_t ctas;           /* persistent CTAs launched                         */
   float kernel_ms;        /* device time of the tile kernel (events)          */
   float total_ms;         /* device time of all kernels of the run            */
+  int64_t h2d_bytes;      /* host-to-device bytes copied by the run           */
+  int64_t d2h_bytes;      /* device-to-host bytes copied by the run           */
+  int32_t launches;       /* kernels launched by the run                      */
+  int32_t reserved;
 } rqa_stats_t;
 
 typedef struct rqa_handle rqa_handle;

@@ -208,6 +208,12 @@ int rqa_batch_run(rqa_batch* b, const rqa_settings* settings, const double* cons
     b->stats.pairs += b->res[q].stats.pairs;
     b->stats.rechecks += b->res[q].stats.rechecks;
   }
+  if (!b->res.empty()) {
+    b->stats.h2d_bytes = b->res[0].stats.h2d_bytes;
+    b->stats.d2h_bytes = b->res[0].stats.d2h_bytes;
+    b->stats.launches = b->res[0].stats.launches;
+    b->stats.ctas = b->res[0].stats.ctas;
+  }
   b->stats.kernel_ms = b->eng->last_tile_ms();
   b->stats.total_ms = b->eng->last_total_ms();
   return rc;

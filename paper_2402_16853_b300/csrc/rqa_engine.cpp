@@ -417,8 +417,12 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   }
   const bool replay = use_graph && graph_ && key == graph_key_;
 
+  int launches = 0;
+  int64_t ctas_total = 0;
   auto enqueue = [&]() -> int {
     cudaError_t e;
+    launches = 0;
+    ctas_total = 0;
     if ((e = cudaEventRecord(ev_[0], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     if ((e = cudaMemsetAsync(arena_ + o_zero, 0, zero_bytes, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemsetAsync");
@@ -430,7 +434,11 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync(series)");
     launch_prepare(d_sd, count, st);
-    if (any_fp32) launch_embed(d_sd, count, max_n_mp, sms_, st);
+    ++launches;
+    if (any_fp32) {
+      launch_embed(d_sd, count, max_n_mp, sms_, st);
+      ++launches;
+    }
     if ((e = cudaEventRecord(ev_[1], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     for (int c = 0; c < ncls; ++c) {
       const int m = std::get<0>(classes[c]), norm = std::get<1>(classes[c]);
@@ -458,9 +466,12 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
                                 dim3(static_cast<unsigned>(grid)), dim3(32 * warps), args, smem,
                                 st)) != cudaSuccess)
         return cuda_fail(e, "tile kernel launch");
+      ++launches;
+      ctas_total += grid;
     }
     if ((e = cudaEventRecord(ev_[2], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     launch_merges(d_sd, count, max_n, sms_, st);
+    launches += 4;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "merge kernels launch");
     if ((e = cudaMemcpyAsync(host_ + h_hist, arena_ + o_hist0, hist_bytes + cnt_bytes,
                              cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -548,6 +559,10 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     s.cols_per_lane = p.z.tc.cols;
     s.kernel_ms = tile_ms_;
     s.total_ms = total_ms_;
+    s.h2d_bytes = static_cast<int64_t>((o_zero - o_sd) + series_bytes);
+    s.d2h_bytes = static_cast<int64_t>(hist_bytes + cnt_bytes + sizeof(SeriesDesc) * count);
+    s.launches = launches;
+    s.ctas = static_cast<int32_t>(ctas_total);
   }
   return first_err;
 }

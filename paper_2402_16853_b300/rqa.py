@@ -77,7 +77,9 @@ class _CStats(ctypes.Structure):
                 ("exact", ctypes.c_int32), ("strip_width", ctypes.c_int32),
                 ("warps_per_cta", ctypes.c_int32), ("cols_per_lane", ctypes.c_int32),
                 ("ctas", ctypes.c_int32), ("kernel_ms", ctypes.c_float),
-                ("total_ms", ctypes.c_float)]
+                ("total_ms", ctypes.c_float), ("h2d_bytes", ctypes.c_int64),
+                ("d2h_bytes", ctypes.c_int64), ("launches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 MEASURE_FIELDS = list(_MEAS_D + _MEAS_I)
