@@ -446,7 +446,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       const int warps = std::get<3>(classes[c]);
       TileFn fn = tile_kernel_for(m, norm, 4, f64);
       if (!fn) return fail(RQA_EINVAL, "no tile kernel for this (m, norm)");
-      const size_t smem = tile_smem_for(m, f64, warps);
+      const size_t smem = tile_smem_for(m, norm, f64, warps, 4);
       if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem))) != cudaSuccess)

@@ -13,7 +13,7 @@ using TileFn = void (*)(const SeriesDesc*, const Item*, int, int*);
 // Fused tile kernel for embedding dimension m (1..10), norm (0 max, 1 L2,
 // 2 L1), columns per lane `cols` (4) and FP64-everywhere or FP32 + recheck.
 TileFn tile_kernel_for(int m, int norm, int cols, bool f64);
-size_t tile_smem_for(int m, bool f64, int warps);
+size_t tile_smem_for(int m, int norm, bool f64, int warps, int cols);
 
 TileFn tile_kernel_norm0(int m, int cols, bool f64);
 TileFn tile_kernel_norm1(int m, int cols, bool f64);

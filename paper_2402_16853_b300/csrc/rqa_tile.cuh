@@ -4,29 +4,30 @@
 // consecutive columns of the upper triangle of the recurrence matrix (the
 // matrix is symmetric, Sect. 4.2 notes the halved degree of parallelism of
 // operator II for it).  Strips are taken from a work queue, longest first.
-// Inside a strip, warp w owns 32*C columns (lane l owns columns
-// col0 + l for C sub-blocks) and walks its rows bottom-up in blocks of 32.
+// Inside a strip, warp w owns 32*C columns (lane l owns columns col0 + l of
+// C sub-blocks) and walks its rows bottom-up in blocks of 32.
 //
 // Per 32 x 32 sub-block the warp fuses the paper's three operators
 // (Sect. 4.2):
-//   I   create_recurrence_matrix -> FP32 distance per pair, the decision
-//       packed by its sign bit into one 32-bit column word per lane; pairs in
-//       the proven FP32 error band are re-decided in FP64;
-//   II  detect_diagonal_lines     -> diagonal words from a bit-reverse,
-//       rotate and 32x32 transpose of the column words, scanned for runs;
+//   I   create_recurrence_matrix -> FP32 distance margin per pair, the
+//       decision taken from its sign bit and packed by a funnel shift into
+//       one 32-bit column word per lane; pairs inside the proven FP32 error
+//       band are re-decided in FP64;
+//   II  detect_diagonal_lines     -> diagonal words from a bit reverse, a
+//       rotate and a 32x32 transpose of the column words, scanned for runs;
 //   III detect_vertical_lines     -> the column words (upper part of full
 //       column j) and the transposed row words (the part of full column i
 //       below the line of identity, by symmetry), scanned for black and
 //       white runs.
-// Lines that cross sub-block borders are carried in registers (down a
-// column, along a diagonal) or passed to the next warp through a shared-
-// memory ring (rows and diagonals leaving the warp to the left).  Runs that
-// touch the strip's own left or right edge are not counted here: their
-// lengths go to small boundary descriptors that the merge kernels join
-// across strips ("carryover buffers", Sect. 4.1).  The run of each full
-// column that touches the line of identity is stored apart and joined by the
-// finalize kernel.  Counts go to shared-memory histograms that are flushed
-// once per strip.
+// Lines that cross sub-block borders are carried in per-warp shared state
+// (down a column, along a diagonal) or passed to the next warp through a
+// shared-memory ring (rows and diagonals leaving the warp to the left).  Runs
+// that touch the strip's own left or right edge are not counted here: their
+// lengths go to boundary descriptors that the merge kernels join across
+// strips (the carryover buffers of Sect. 4.1).  The run of each full column
+// that touches the line of identity is stored apart and joined by the
+// finalize kernel.  Counts go to shared-memory histograms flushed once per
+// strip.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -52,17 +53,26 @@ constexpr uint32_t ST_FLAG = 1u << 29;
 constexpr uint32_t ST_DONE = 1u << 30;
 constexpr uint32_t DG_EDGE = 1u << 28;
 
+// Status word value for an internal inconsistency (a line length outside
+// 1..n); the entry point reports it as RQA_ECUDA.
+constexpr unsigned long long STATUS_INTERNAL = 5ull;
+
+// Bits [0, k) set, k clamped to [0, 32] (one BMSK instruction).
 __device__ __forceinline__ uint32_t lowmask(int k) {
-  return k >= 32 ? FULL : (k <= 0 ? 0u : ((1u << k) - 1u));
+  uint32_t r;
+  asm("bmsk.clamp.b32 %0, %1, %2;" : "=r"(r) : "r"(0), "r"(k < 0 ? 0 : k));
+  return r;
 }
 
-__device__ __forceinline__ int clamp32(int64_t v) {
-  return v < 0 ? 0 : (v > 32 ? 32 : (int)v);
-}
+__device__ __forceinline__ int clamp32(int v) { return v < 0 ? 0 : (v > 32 ? 32 : v); }
+
+// Position of the highest set bit (x != 0).
+__device__ __forceinline__ int msb(uint32_t x) { return 31 - __clz(x); }
 
 // 32 x 32 bit transpose across a warp: lane r holds row r (bit c = A[r][c]);
-// on return lane c holds bit r = A[r][c].  Five shuffle stages, each swapping
-// the off-diagonal blocks of 2j x 2j blocks.
+// on return lane c holds bit r = A[r][c].  Five stages; each swaps the
+// off-diagonal j x j blocks of every 2j x 2j block with one shuffle, one
+// rotate and one three-input logic operation.
 __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 #pragma unroll
   for (int j = 16; j >= 1; j >>= 1) {
@@ -71,85 +81,100 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
                      : j == 4  ? 0x0F0F0F0Fu
                      : j == 2  ? 0x33333333u
                                : 0x55555555u;
+    const bool hi = (lane & j) != 0;
+    const uint32_t keep = hi ? ~m : m;
     const uint32_t y = __shfl_xor_sync(FULL, x, j);
-    x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y << j) & ~m));
+    const uint32_t rot = __funnelshift_l(y, y, hi ? 32 - j : j);
+    x = (x & keep) | (rot & ~keep);
   }
   return x;
 }
 
-// Status word value for an internal inconsistency (a line length outside
-// 1..n); the entry point reports it as RQA_ECUDA.
-constexpr unsigned long long STATUS_INTERNAL = 5ull;
-
-// Shared-memory histogram with a global fallback for long lines.  A length
-// outside 1..n is never written; it marks the series as failed instead.
+// Histogram sink: shared-memory bins for short lines, global atomics for
+// long ones.  A length outside 1..n is never written; it marks the series
+// as failed instead.
 struct HistSink {
   uint32_t* sh;              // [3][HB]
   unsigned long long* gl;    // [3][n+1]
-  int64_t stride;            // n + 1
+  uint32_t n;
   unsigned long long* status;
   __device__ __forceinline__ void add(int type, uint32_t len) const {
-    if (len < (uint32_t)HB && len > 0)
+    if (len - 1u < (uint32_t)(HB - 1))
       atomicAdd(&sh[type * HB + len], 1u);
-    else if (len > 0 && (int64_t)len < stride)
-      atomicAdd(&gl[type * stride + len], 1ull);
+    else
+      slow(type, len);
+  }
+  __device__ __noinline__ void slow(int type, uint32_t len) const {
+    if (len > 0 && len <= n)
+      atomicAdd(&gl[(size_t)type * (n + 1) + len], 1ull);
     else
       atomicExch(status, STATUS_INTERNAL);
   }
+  // vertical (black, colour 1) or white vertical (colour 0)
+  __device__ __forceinline__ void add2(uint32_t colour, uint32_t len) const {
+    add(colour ? HIST_VERT : HIST_WHITE, len);
+  }
 };
 
-// Scan cells hi..lo (descending bit index) of word x with two colours,
-// continuing run state st.  close(colour, len, flag) is called for each run
-// that ends inside the range; the open run is returned.
-template <class F>
-__device__ __forceinline__ uint32_t scan2(uint32_t x, int hi, int lo, uint32_t st,
-                                          F&& close) {
+// Scan the two-colour cells hi..lo (descending bit index) of x, continuing
+// run state st.  first(colour, len) receives the first run that ends here if
+// st carries the flag, emit(colour, len) every other run that ends here; the
+// run left open at lo is returned.
+template <class E, class F>
+__device__ __forceinline__ uint32_t scan2(uint32_t x, int hi, int lo, uint32_t st, E&& emit,
+                                          F&& first) {
+  uint32_t cl = st & ST_LEN;
+  const uint32_t cc = (st >> 28) & 1u;
+  uint32_t fl = (st >> 29) & 1u;
   uint32_t col = (x >> hi) & 1u;
-  uint32_t len = st & ST_LEN;
-  uint32_t flag = (st & ST_FLAG) ? 1u : 0u;
-  if (len != 0 && (((st & ST_COLOUR) ? 1u : 0u) != col)) {
-    close((st & ST_COLOUR) ? 1u : 0u, len, flag);
-    len = 0;
-    flag = 0;
+  if (cl != 0 && cc != col) {  // the carried run ends before cell hi
+    if (fl) first(cc, cl); else emit(cc, cl);
+    fl = 0;
+    cl = 0;
   }
   uint32_t T = (x ^ (x << 1)) & lowmask(hi + 1) & ~lowmask(lo + 1);
   int top = hi;
-  while (T) {
-    const int p = 31 - __clz(T);
-    len += (uint32_t)(top - p + 1);
-    close(col, len, flag);
-    flag = 0;
-    len = 0;
+  if (T) {
+    int p = msb(T);
+    const uint32_t len = cl + (uint32_t)(top - p + 1);
+    if (fl) first(col, len); else emit(col, len);
+    fl = 0;
+    cl = 0;
     col ^= 1u;
     top = p - 1;
-    T &= lowmask(p);
+    T ^= 1u << p;
+    while (T) {
+      p = msb(T);
+      emit(col, (uint32_t)(top - p + 1));
+      col ^= 1u;
+      top = p - 1;
+      T ^= 1u << p;
+    }
   }
-  len += (uint32_t)(top - lo + 1);
-  return len | (col ? ST_COLOUR : 0u) | (flag ? ST_FLAG : 0u);
+  return (cl + (uint32_t)(top - lo + 1)) | (col << 28) | (fl << 29);
 }
 
-// Scan the black runs of cells hi..lo (descending) of x, continuing diagonal
-// state st.  first(len) is called when the run that touches the strip's edge
-// ends (len may be 0), emit(len) for every other run that ends inside.
-template <class FA, class FE>
-__device__ __forceinline__ uint32_t scan_black(uint32_t x, int hi, int lo, uint32_t st,
-                                               FA&& first, FE&& emit) {
-  const uint32_t seg = lowmask(hi + 1) & ~lowmask(lo);
+// Scan the black runs of cells hi..lo (descending; x already restricted to
+// seg, their mask), continuing diagonal state st.  first(len) receives the
+// run that touches the strip's edge when it ends (len may be 0), emit(len)
+// every other run that ends inside.
+template <class E, class F>
+__device__ __forceinline__ uint32_t scan_black(uint32_t x, uint32_t seg, int hi, int lo,
+                                               uint32_t st, E&& emit, F&& first) {
   const uint32_t z = ~x & seg;
-  uint32_t len = st & ST_LEN;
-  const bool edge = (st & DG_EDGE) != 0;
-  if (z == 0) return (len + (uint32_t)(hi - lo + 1)) | (edge ? DG_EDGE : 0u);
-  const int ptop = 31 - __clz(z);
-  const uint32_t fl = len + (uint32_t)(hi - ptop);
-  if (edge)
-    first(fl);
-  else if (fl)
-    emit(fl);
+  const uint32_t cl = st & ST_LEN;
+  if (z == 0) return (cl + (uint32_t)(hi - lo + 1)) | (st & DG_EDGE);
+  const int ptop = msb(z);
+  const uint32_t f = cl + (uint32_t)(hi - ptop);
+  if (st & DG_EDGE)
+    first(f);
+  else if (f)
+    emit(f);
   const int pbot = __ffs(z) - 1;
-  uint32_t mid = x & seg & lowmask(ptop) & ~lowmask(pbot + 1);
+  uint32_t mid = x & lowmask(ptop) & ~lowmask(pbot + 1);
   while (mid) {
-    const int h = 31 - __clz(mid);
-    const int zz = 31 - __clz(z & lowmask(h));
+    const int h = msb(mid);
+    const int zz = msb(z & lowmask(h));
     emit((uint32_t)(h - zz));
     mid &= lowmask(zz);
   }
@@ -182,6 +207,32 @@ __device__ __forceinline__ float pair_margin(const float* xr, const float* xc, f
     for (int k = 0; k < M; ++k) mx = fmaxf(mx, fabsf(__fsub_rn(xr[k], xc[k])));
     return __fsub_rn(thr, mx);
   }
+}
+
+// Packed FP32x2 helpers (sm_100 and later): two columns per instruction.
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
 }
 
 // Exact FP64 decision, in the operation order of the specification (no
@@ -242,37 +293,52 @@ __device__ __forceinline__ bool spin_until_ge(volatile int* ctr, int target,
   return true;
 }
 
-// Shared-memory bytes of the tile kernel.
-template <int M, bool F64>
-__host__ __device__ constexpr int tile_row_floats() {
-  return F64 ? M : ((M + 3) / 4) * 4;
+// Row buffer layout: FP32 rows hold each coordinate twice (x0 x0 x1 x1 ...)
+// for the packed L2 path, once otherwise; FP64 rows hold m doubles.
+template <int M, int NORM, bool F64>
+__host__ __device__ constexpr int tile_row_elems() {
+  return F64 ? M : (NORM == 1 ? ((2 * M + 3) / 4) * 4 : ((M + 3) / 4) * 4);
 }
-inline size_t tile_smem_bytes(int warps, int row_elems, int elem_bytes) {
-  return (size_t)3 * HB * 4 + (size_t)warps * 32 * row_elems * elem_bytes +
-         (size_t)(warps > 1 ? warps - 1 : 0) * RING * 64 * 4 + (size_t)2 * warps * 4 + 16;
+
+// Shared-memory bytes of the tile kernel for a launch shape.
+inline size_t tile_smem_bytes(int warps, int row_elems, int elem_bytes, int cols) {
+  return (size_t)3 * HB * 4                                    // histograms
+         + (size_t)warps * 32 * row_elems * elem_bytes          // row vectors
+         + (size_t)warps * 3 * cols * 32 * 4                    // per-warp column state
+         + (size_t)(warps > 1 ? warps - 1 : 0) * RING * 64 * 4  // carry rings
+         + (size_t)2 * warps * 4 + 16;
 }
 
 // ------------------------------------------------------------------ kernel
 template <int M, int NORM, int C, bool F64>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, int nitems,
             int* __restrict__ queue) {
   using T = typename std::conditional<F64, double, float>::type;
-  constexpr int MP = tile_row_floats<M, F64>();
+  constexpr int RE = tile_row_elems<M, NORM, F64>();
+  constexpr bool PACKED = !F64 && NORM == 1 && (C % 2 == 0);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NW = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 
   uint32_t* sh_hist = reinterpret_cast<uint32_t*>(smem_raw);
-  T* rowbuf = reinterpret_cast<T*>(sh_hist + 3 * HB) + warp * 32 * MP;
-  T* rowbuf_end = reinterpret_cast<T*>(sh_hist + 3 * HB) + NW * 32 * MP;
-  uint32_t* ring = reinterpret_cast<uint32_t*>(rowbuf_end);
+  T* rowbuf = reinterpret_cast<T*>(sh_hist + 3 * HB) + warp * 32 * RE;
+  uint32_t* wstate =
+      reinterpret_cast<uint32_t*>(reinterpret_cast<T*>(sh_hist + 3 * HB) + NW * 32 * RE);
+  uint32_t* Rw_s = wstate + warp * 3 * C * 32;   // recurrence words  [C][32]
+  uint32_t* cst_s = Rw_s + C * 32;               // column run state  [C][32]
+  uint32_t* dU_s = cst_s + C * 32;               // diagonal up carry [C][32]
+  uint32_t* ring = wstate + NW * 3 * C * 32;
   volatile int* prod = reinterpret_cast<volatile int*>(ring + (NW > 1 ? NW - 1 : 0) * RING * 64);
   volatile int* cons = prod + NW;
   __shared__ int s_item;
   __shared__ int s_skip;
   __shared__ volatile int s_abort;
+
+  // per-lane diagonal segment masks (lane d: lower segment bits d-1..0)
+  const uint32_t segL = lowmask(lane);
+  const uint32_t segU = ~segL;
 
   for (;;) {
     __syncthreads();
@@ -292,71 +358,87 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
     if (s_skip) continue;  // the series already failed (non-finite input or timeout)
     unsigned long long rechecks = 0;
     const Item wi = items[it];
-    const SeriesDesc& S = sd[wi.series];
-    const int64_t n = S.n;
-    const int64_t SW = S.sw;
-    const int64_t J1 = n - (int64_t)wi.strip * SW;             // strip: [J1-SW, J1)
+    const SeriesDesc* Sp = sd + wi.series;
+    const int n = (int)Sp->n;
+    const int SW = Sp->sw;
+    const int tau = Sp->tau;
+    const int wtheiler = Sp->w;
+    const double* __restrict__ sser = Sp->s;
+    const float* __restrict__ xe = Sp->xe;
+    const int mp = Sp->mp;
+    const double eps = Sp->eps;
+    uint32_t* __restrict__ colend = Sp->colend;
+    uint16_t* __restrict__ row_a = Sp->row_a;
+    uint16_t* __restrict__ row_z = Sp->row_z;
+    uint16_t* __restrict__ dia_a = Sp->dia_a;
+    uint16_t* __restrict__ dia_z = Sp->dia_z;
+    const int J1 = n - wi.strip * SW;                 // strip: [J1-SW, J1)
     const int64_t off = strip_offset(n, SW, wi.strip);
-    const int64_t jw1 = J1 - (int64_t)warp * 32 * C;           // warp: [jw0, jw1)
-    const int64_t jw0 = jw1 - 32 * C;
-    const int64_t wl_geo = (J1 - 2) / (32 * C);
-    const int wlast = (int)(wl_geo < NW - 1 ? wl_geo : NW - 1);
-    const HistSink hs{sh_hist, S.hist, n + 1, &S.counters[CNT_STATUS]};
-    const int wtheiler = S.w;
+    const int jw1 = J1 - warp * 32 * C;              // warp: [jw0, jw1)
+    const int jw0 = jw1 - 32 * C;
+    const int wl_geo = (J1 - 2) / (32 * C);
+    const int wlast = wl_geo < NW - 1 ? wl_geo : NW - 1;
+    const HistSink hs{sh_hist, Sp->hist, (uint32_t)n, &Sp->counters[CNT_STATUS]};
 
     if (warp <= wlast) {
       const bool leftmost = warp == wlast;
-      const int64_t jmax = jw1 - 1;
-      const int bhi = (int)((jmax - 1) >> 5);
-      const int bhi_left = leftmost ? -1 : (int)((jmax - 32 * C - 1) >> 5);
+      const int jmax = jw1 - 1;
+      const int bhi = (jmax - 1) >> 5;
+      const int bhi_left = leftmost ? -1 : ((jmax - 32 * C - 1) >> 5);
       uint32_t* ring_in = warp > 0 ? ring + (warp - 1) * RING * 64 : nullptr;
       uint32_t* ring_out = !leftmost ? ring + warp * RING * 64 : nullptr;
       int seq_in = 0, seq_out = 0;
 
-      // Column vectors of this lane's C columns stay in registers for the strip.
-      T xc[C][M];
+      // Column vectors of this lane's C columns stay in registers (packed in
+      // pairs of columns on the L2 path).
+      constexpr int CX = PACKED ? 1 : C;
+      constexpr int CP = PACKED ? C / 2 : 1;
+      T xc[CX][M];
+      unsigned long long xc2[CP][M];
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const int64_t j = jw0 + 32 * c + lane;
+        const int j = jw0 + 32 * c + lane;
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-          if constexpr (F64)
-            xc[c][k] = j >= 0 ? (T)S.s[j + (int64_t)k * S.tau] : (T)0;
-          else
-            xc[c][k] = j >= 0 ? (T)S.xe[j * S.mp + k] : (T)0;
+          if constexpr (F64) {
+            xc[c][k] = j >= 0 ? sser[j + k * tau] : 0.0;
+          } else if constexpr (PACKED) {
+            if (c % 2 == 1) {
+              const int j0 = j - 32;
+              xc2[c / 2][k] = f2_pack(j0 >= 0 ? xe[(int64_t)j0 * mp + k] : 0.f,
+                                      j >= 0 ? xe[(int64_t)j * mp + k] : 0.f);
+            }
+          } else {
+            xc[c][k] = j >= 0 ? xe[(int64_t)j * mp + k] : 0.f;
+          }
         }
+        cst_s[c * 32 + lane] = ST_FLAG;
+        dU_s[c * 32 + lane] = 0;
       }
-      uint32_t cst[C];   // column run state (first-run flag set)
-      uint32_t dU[C];    // diagonal run leaving each sub-block upwards
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        cst[c] = ST_FLAG;
-        dU[c] = 0;
-      }
-      const float thr = S.thr;
-      const float band = S.band;
+      const float thr = Sp->thr;
+      const float band = Sp->band;
       bool ok = true;
 
       for (int b = bhi; b >= 0 && ok; --b) {
-        const int64_t r0 = (int64_t)b << 5;
+        const int r0 = b << 5;
         {  // row vectors of rows r0 .. r0+31 into this warp's buffer
-          const int64_t i = r0 + lane;
+          const int i = r0 + lane;
 #pragma unroll
-          for (int k = 0; k < MP; ++k) {
+          for (int k = 0; k < RE; ++k) {
             T v = (T)0;
-            if (i < n && k < M) {
-              if constexpr (F64)
-                v = S.s[i + (int64_t)k * S.tau];
-              else
-                v = S.xe[i * S.mp + k];
+            if constexpr (F64) {
+              if (i < n && k < M) v = sser[i + k * tau];
+            } else if constexpr (NORM == 1) {
+              if (i < n && (k >> 1) < M) v = xe[(int64_t)i * mp + (k >> 1)];
+            } else {
+              if (i < n && k < M) v = xe[(int64_t)i * mp + k];
             }
-            rowbuf[lane * MP + k] = v;
+            rowbuf[lane * RE + k] = v;
           }
         }
         __syncwarp();
 
         // ---- operator I: recurrence words (bit t = row r0 + t) per column
-        uint32_t Rw[C];
         if constexpr (!F64) {
           uint32_t Nw[C];
           float mn[C];
@@ -365,72 +447,107 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             Nw[c] = 0;
             mn[c] = __int_as_float(0x7f800000);
           }
+          if constexpr (PACKED) {
+            // L2, two columns per packed op.  Accumulate -thr + sum d^2, the
+            // exact negation of pair_margin() (round-to-nearest is symmetric),
+            // whose sign bit is 1 for a recurrence.  An exact zero (a tie) is
+            // inside the band and re-decided below.
+            const unsigned long long nthr2 = f2_pack(-thr, -thr);
 #pragma unroll 4
-          for (int t = 31; t >= 0; --t) {
-            float xr[MP];
+            for (int t = 31; t >= 0; --t) {
+              unsigned long long xr2[M];
+              const float* rb = reinterpret_cast<const float*>(rowbuf) + t * RE;
 #pragma unroll
-            for (int k = 0; k < MP; k += 4) {
-              const float4 v = *reinterpret_cast<const float4*>(
-                  reinterpret_cast<const float*>(rowbuf) + t * MP + k);
-              xr[k] = v.x;
-              if (k + 1 < MP) xr[k + 1] = v.y;
-              if (k + 2 < MP) xr[k + 2] = v.z;
-              if (k + 3 < MP) xr[k + 3] = v.w;
+              for (int k = 0; k < M; ++k)
+                xr2[k] = *reinterpret_cast<const unsigned long long*>(rb + 2 * k);
+#pragma unroll
+              for (int c = 0; c < C / 2; ++c) {
+                unsigned long long acc = nthr2;
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                  const unsigned long long d = f2_sub(xr2[k], xc2[c][k]);
+                  acc = f2_fma(d, d, acc);
+                }
+                float a0, a1;
+                f2_unpack(acc, a0, a1);
+                Nw[2 * c] = __funnelshift_l(__float_as_uint(a0), Nw[2 * c], 1);
+                Nw[2 * c + 1] = __funnelshift_l(__float_as_uint(a1), Nw[2 * c + 1], 1);
+                mn[2 * c] = min3f(mn[2 * c], fabsf(a0), fabsf(a1));
+              }
             }
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-              const float acc = pair_margin<M, NORM>(xr, (const float*)xc[c], thr);
-              Nw[c] = __funnelshift_l(__float_as_uint(acc), Nw[c], 1);
-              mn[c] = fminf(mn[c], fabsf(acc));
+            for (int c = 0; c < C / 2; ++c) mn[2 * c + 1] = mn[2 * c];
+          } else {
+#pragma unroll 4
+            for (int t = 31; t >= 0; --t) {
+              float xr[M];
+              const float* rb = reinterpret_cast<const float*>(rowbuf) + t * RE;
+#pragma unroll
+              for (int k = 0; k < M; ++k) xr[k] = rb[k];
+#pragma unroll
+              for (int c = 0; c < C; ++c) {
+                const float acc = pair_margin<M, NORM>(xr, (const float*)xc[c], thr);
+                Nw[c] = __funnelshift_l(__float_as_uint(acc), Nw[c], 1);
+                mn[c] = fminf(mn[c], fabsf(acc));
+              }
             }
           }
 #pragma unroll
           for (int c = 0; c < C; ++c) {
-            const int64_t j = jw0 + 32 * c + lane;
-            const uint32_t live = j < 0 ? 0u
-                                        : lowmask(clamp32(j - r0)) &
-                                              lowmask(clamp32(j - wtheiler - r0 + 1));
-            uint32_t R = ~Nw[c] & live;
+            const int j = jw0 + 32 * c + lane;
+            const uint32_t live =
+                j < 0 ? 0u : lowmask(j - r0) & lowmask(j - wtheiler - r0 + 1);
+            // packed: sign bit = recurrent; scalar: sign bit = not recurrent
+            uint32_t R = (PACKED ? Nw[c] : ~Nw[c]) & live;
             if (mn[c] <= band && live) {
               // near-radius pairs: re-decide in FP64 with the exact order
               uint32_t todo = live;
               while (todo) {
                 const int t = __ffs(todo) - 1;
                 todo &= todo - 1;
-                float xr[M];
+                float xr[M], xcc[M];
+                const float* rb = reinterpret_cast<const float*>(rowbuf) + t * RE;
 #pragma unroll
-                for (int k = 0; k < M; ++k)
-                  xr[k] = reinterpret_cast<const float*>(rowbuf)[t * MP + k];
-                const float acc = pair_margin<M, NORM>(xr, (const float*)xc[c], thr);
+                for (int k = 0; k < M; ++k) {
+                  xr[k] = PACKED ? rb[2 * k] : rb[k];
+                  if constexpr (PACKED) {
+                    float a, bb;
+                    f2_unpack(xc2[c / 2][k], a, bb);
+                    xcc[k] = (c % 2) ? bb : a;
+                  } else {
+                    xcc[k] = (float)xc[c][k];
+                  }
+                }
+                const float acc = pair_margin<M, NORM>(xr, xcc, thr);
                 if (fabsf(acc) <= band) {
-                  const bool r = exact_decision<NORM>(S.s, r0 + t, j, M, S.tau, S.eps);
+                  const bool r = exact_decision<NORM>(sser, r0 + t, j, M, tau, eps);
                   R = r ? (R | (1u << t)) : (R & ~(1u << t));
                   ++rechecks;
                 }
               }
             }
-            Rw[c] = R;
+            Rw_s[c * 32 + lane] = R;
           }
         } else {
+          uint32_t Rf[C];
 #pragma unroll
-          for (int c = 0; c < C; ++c) Rw[c] = 0;
+          for (int c = 0; c < C; ++c) Rf[c] = 0;
           for (int t = 31; t >= 0; --t) {
             double xr[M];
 #pragma unroll
-            for (int k = 0; k < M; ++k) xr[k] = reinterpret_cast<const double*>(rowbuf)[t * MP + k];
+            for (int k = 0; k < M; ++k) xr[k] = reinterpret_cast<const double*>(rowbuf)[t * RE + k];
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-              const bool r = exact_decision_regs<M, NORM>(xr, (const double*)xc[c], S.eps);
-              Rw[c] = (Rw[c] << 1) | (r ? 1u : 0u);
+              const bool r = exact_decision_regs<M, NORM>(xr, (const double*)xc[c], eps);
+              Rf[c] = (Rf[c] << 1) | (r ? 1u : 0u);
             }
           }
 #pragma unroll
           for (int c = 0; c < C; ++c) {
-            const int64_t j = jw0 + 32 * c + lane;
-            const uint32_t live = j < 0 ? 0u
-                                        : lowmask(clamp32(j - r0)) &
-                                              lowmask(clamp32(j - wtheiler - r0 + 1));
-            Rw[c] &= live;
+            const int j = jw0 + 32 * c + lane;
+            const uint32_t live =
+                j < 0 ? 0u : lowmask(j - r0) & lowmask(j - wtheiler - r0 + 1);
+            Rw_s[c * 32 + lane] = Rf[c] & live;
           }
         }
         __syncwarp();
@@ -454,43 +571,41 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           ++seq_in;
         }
 
-        const int64_t irow = r0 + lane;
-#pragma unroll
+        const int irow = r0 + lane;
+        const bool row_valid = irow <= J1 - 2;
+#pragma unroll 1
         for (int c = C - 1; c >= 0; --c) {
-          const int64_t col0 = jw0 + 32 * c;
-          const int64_t j = col0 + lane;
-          const uint32_t R = Rw[c];
+          const int col0 = jw0 + 32 * c;
+          const int j = col0 + lane;
+          const uint32_t R = Rw_s[c * 32 + lane];
 
           // ---- operator III, upper part of full column j (rows < j)
           {
             const int vt = j < 0 ? 0 : clamp32(j - r0);
             if (vt > 0) {
-              cst[c] = scan2(R, vt - 1, 0, cst[c], [&](uint32_t col, uint32_t len, uint32_t first) {
-                if (first)
-                  S.colend[j] = len | (col << 31);
-                else
-                  hs.add(col ? HIST_VERT : HIST_WHITE, len);
-              });
+              cst_s[c * 32 + lane] = scan2(
+                  R, vt - 1, 0, cst_s[c * 32 + lane],
+                  [&](uint32_t col, uint32_t len) { hs.add2(col, len); },
+                  [&](uint32_t col, uint32_t len) { colend[j] = len | (col << 31); });
             }
           }
 
           // ---- operator III, lower part of full column irow = upper row irow
           {
             const uint32_t RW = transpose32(R, lane);
-            const int64_t lo = irow + 1 - col0;  // first valid bit of the row
-            if (lo <= 31 && !(rst & ST_DONE) && irow <= J1 - 2) {
-              const int lo_c = lo < 0 ? 0 : (int)lo;
-              rst = scan2(RW, 31, lo_c, rst, [&](uint32_t col, uint32_t len, uint32_t edge) {
-                if (edge)
-                  S.row_a[off + irow] = (uint16_t)((len << 1) | col);
-                else
-                  hs.add(col ? HIST_VERT : HIST_WHITE, len);
-              });
+            const int lo = irow + 1 - col0;  // first valid bit of the row
+            if (lo <= 31 && !(rst & ST_DONE) && row_valid) {
+              const int lo_c = lo < 0 ? 0 : lo;
+              rst = scan2(
+                  RW, 31, lo_c, rst, [&](uint32_t col, uint32_t len) { hs.add2(col, len); },
+                  [&](uint32_t col, uint32_t len) {
+                    row_a[off + irow] = (uint16_t)((len << 1) | col);
+                  });
               if (lo >= 0) {  // the row ends here, at column irow + 1
-                const uint32_t len = rst & ST_LEN, col = (rst & ST_COLOUR) ? 1u : 0u;
-                const uint32_t same = (rst & ST_FLAG) ? 1u : 0u;
-                S.row_z[off + irow] = (uint16_t)((len << 2) | (same << 1) | col);
-                if (same) S.row_a[off + irow] = 0;
+                const uint32_t len = rst & ST_LEN, col = (rst >> 28) & 1u;
+                const uint32_t same = (rst >> 29) & 1u;
+                row_z[off + irow] = (uint16_t)((len << 2) | (same << 1) | col);
+                if (same) row_a[off + irow] = 0;
                 rst = ST_DONE;
               }
             }
@@ -498,49 +613,47 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
 
           // ---- operator II, diagonal segments (lane d)
           {
-            uint32_t Rr = __brev(R);
-            Rr = __funnelshift_r(Rr, Rr, 31 - lane);
+            const uint32_t rb = __brev(R);
+            const uint32_t Rr = __funnelshift_r(rb, rb, 31 - lane);
             const uint32_t D = transpose32(Rr, lane);
             const int d = lane;
             // lower segment: bits d-1..0, diagonal k = col0 - r0 + d - 32,
-            // continues the upper segment of the block below (dU[c]).
-            const int64_t klo = col0 - r0 + d - 32;
-            uint32_t Lnext = dU[c];
+            // continues the upper segment of the block below.
+            const int klo = col0 - r0 + d - 32;
+            const uint32_t du = dU_s[c * 32 + lane];
+            uint32_t Lnext = du;
             if (d > 0) {
               Lnext = scan_black(
-                  D, d - 1, 0, dU[c],
+                  D & segL, segL, d - 1, 0, du, [&](uint32_t len) { hs.add(HIST_DIAG, len); },
                   [&](uint32_t len) {
-                    if (klo >= 1) S.dia_a[off + klo - 1] = (uint16_t)len;
-                  },
-                  [&](uint32_t len) { hs.add(HIST_DIAG, len); });
+                    if (klo >= 1) dia_a[off + klo - 1] = (uint16_t)len;
+                  });
             }
-            // upper segment: bits 31..d, diagonal k = col0 - r0 + d, continues
-            // the lower segment of the sub-block to the right (dL).
-            const int64_t kup = col0 - r0 + d;
-            dU[c] = scan_black(
-                D, 31, d, dL,
+            // upper segment: bits 31..d, diagonal k = col0 - r0 + d,
+            // continues the lower segment of the sub-block to the right.
+            const int kup = col0 - r0 + d;
+            dU_s[c * 32 + lane] = scan_black(
+                D & segU, segU, 31, d, dL, [&](uint32_t len) { hs.add(HIST_DIAG, len); },
                 [&](uint32_t len) {
-                  if (kup >= 1) S.dia_a[off + kup - 1] = (uint16_t)len;
-                },
-                [&](uint32_t len) { hs.add(HIST_DIAG, len); });
+                  if (kup >= 1) dia_a[off + kup - 1] = (uint16_t)len;
+                });
             dL = Lnext;
           }
         }
 
         // ---- carries leaving to the left
         if (leftmost) {
-          if (!(rst & ST_DONE) && irow <= J1 - 2) {
-            const uint32_t len = rst & ST_LEN, col = (rst & ST_COLOUR) ? 1u : 0u;
-            const uint32_t same = (rst & ST_FLAG) ? 1u : 0u;
+          if (!(rst & ST_DONE) && row_valid) {
+            const uint32_t len = rst & ST_LEN, col = (rst >> 28) & 1u;
+            const uint32_t same = (rst >> 29) & 1u;
             if (len > 0) {
-              S.row_z[off + irow] = (uint16_t)((len << 2) | (same << 1) | col);
-              if (same) S.row_a[off + irow] = 0;
+              row_z[off + irow] = (uint16_t)((len << 2) | (same << 1) | col);
+              if (same) row_a[off + irow] = 0;
             }
           }
-          const int64_t kx = jw0 - r0 + lane - 32;  // diagonal leaving through the left edge
-          if (kx >= 1) {
-            S.dia_z[off + kx - 1] = (uint16_t)((dL & ST_LEN) | ((dL & DG_EDGE) ? 0x8000u : 0u));
-          }
+          const int kx = jw0 - r0 + lane - 32;  // diagonal leaving through the left edge
+          if (kx >= 1)
+            dia_z[off + kx - 1] = (uint16_t)((dL & ST_LEN) | ((dL & DG_EDGE) ? 0x8000u : 0u));
         } else if (b <= bhi_left) {
           if (lane == 0) ok = spin_until_ge(cons + (warp + 1), seq_out - RING + 1, &s_abort);
           ok = __shfl_sync(FULL, ok, 0);
@@ -557,38 +670,37 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
 
       if (ok) {
         // ---- top border: close column runs, record diagonal ends (row 0)
-#pragma unroll
+#pragma unroll 1
         for (int c = 0; c < C; ++c) {
-          const int64_t j = jw0 + 32 * c + lane;
+          const int j = jw0 + 32 * c + lane;
           if (j >= 1) {
-            const uint32_t st = cst[c];
-            const uint32_t len = st & ST_LEN, col = (st & ST_COLOUR) ? 1u : 0u;
+            const uint32_t st = cst_s[c * 32 + lane];
+            const uint32_t len = st & ST_LEN, col = (st >> 28) & 1u;
             if (len > 0) {
               if (st & ST_FLAG)
-                S.colend[j] = len | (col << 31);
+                colend[j] = len | (col << 31);
               else
-                hs.add(col ? HIST_VERT : HIST_WHITE, len);
+                hs.add2(col, len);
             }
-            // diagonal k = j ends at (0, j)
-            S.dia_z[off + j - 1] =
-                (uint16_t)((dU[c] & ST_LEN) | ((dU[c] & DG_EDGE) ? 0x8000u : 0u));
+            const uint32_t du = dU_s[c * 32 + lane];  // diagonal k = j ends at (0, j)
+            dia_z[off + j - 1] = (uint16_t)((du & ST_LEN) | ((du & DG_EDGE) ? 0x8000u : 0u));
           }
         }
       }
     }
     __syncthreads();
     if (s_abort && threadIdx.x == 0)
-      atomicExch(&S.counters[CNT_STATUS], 6ull /* RQA_ETIMEOUT */);
+      atomicExch(&Sp->counters[CNT_STATUS], 6ull /* RQA_ETIMEOUT */);
     // flush the strip's histograms
-    const int64_t stride = n + 1;
+    const int64_t stride = (int64_t)n + 1;
     for (int q = threadIdx.x; q < 3 * HB; q += blockDim.x) {
       const uint32_t v = sh_hist[q];
-      if (v) atomicAdd(&S.hist[(q / HB) * stride + (q % HB)], (unsigned long long)v);
+      if (v) atomicAdd(&Sp->hist[(q / HB) * stride + (q % HB)], (unsigned long long)v);
     }
     // rechecks of this strip: one atomic per warp
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rechecks += __shfl_xor_sync(FULL, rechecks, o);
-    if (lane == 0 && rechecks) atomicAdd(&S.counters[CNT_RECHECKS], rechecks);
+    if (lane == 0 && rechecks) atomicAdd(&Sp->counters[CNT_RECHECKS], rechecks);
   }
 }
 

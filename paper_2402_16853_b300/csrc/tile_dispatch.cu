@@ -13,9 +13,9 @@ TileFn tile_kernel_for(int m, int norm, int cols, bool f64) {
   }
 }
 
-size_t tile_smem_for(int m, bool f64, int warps) {
-  const int row_elems = f64 ? m : ((m + 3) / 4) * 4;
-  return tile_smem_bytes(warps, row_elems, f64 ? 8 : 4);
+size_t tile_smem_for(int m, int norm, bool f64, int warps, int cols) {
+  const int row_elems = f64 ? m : (norm == 1 ? ((2 * m + 3) / 4) * 4 : ((m + 3) / 4) * 4);
+  return tile_smem_bytes(warps, row_elems, f64 ? 8 : 4, cols);
 }
 
 }  // namespace rqa
