@@ -181,6 +181,113 @@ __device__ __forceinline__ uint32_t scan_black(uint32_t x, uint32_t seg, int hi,
   return (uint32_t)(pbot - lo);
 }
 
+// Lines of length 1..3 are counted without emitting them one by one: 16-bit
+// fields packed two per register, added to the histograms every
+// FLUSH_BLOCKS blocks (at most 128 per field per block, so no field wraps).
+struct ShortCounts {
+  uint32_t v12;   // vertical black: length 1 | length 2 << 16
+  uint32_t v3w1;  // vertical black length 3 | white length 1 << 16
+  uint32_t w23;   // white: length 2 | length 3 << 16
+  uint32_t d12;   // diagonal: length 1 | length 2 << 16
+  uint32_t d3;    // diagonal: length 3
+};
+constexpr int FLUSH_BLOCKS = 256;
+
+// Two-colour scan of a full word (cells 31 .. 0 in scan order), same
+// contract as scan2(x, 31, 0, ...).  Runs that touch neither cell 31 nor
+// cell 0 are interior: with T the transition mask, an interior run starts
+// (lowest cell q) at every transition below the topmost one and its length
+// is the distance to the next transition above q, so the interior runs of
+// length 1, 2 and 3 are popcounts of T against T shifted by 1, 2 and 3.
+// Only longer interior runs and the two runs touching the word's ends are
+// passed to emit / first individually.
+template <class E, class F>
+__device__ __forceinline__ uint32_t scan2_full(uint32_t x, uint32_t st, ShortCounts& sc,
+                                               E&& emit, F&& first) {
+  const uint32_t T = (x ^ (x << 1)) & 0xFFFFFFFEu;
+  uint32_t cl = st & ST_LEN;
+  const uint32_t cc = (st >> 28) & 1u;
+  uint32_t fl = (st >> 29) & 1u;
+  const uint32_t ctop = x >> 31;
+  if (cl != 0 && cc != ctop) {
+    if (fl) first(cc, cl); else emit(cc, cl);
+    fl = 0;
+    cl = 0;
+  }
+  if (T == 0) return (cl + 32u) | (ctop << 28) | (fl << 29);
+  const int ptop = msb(T);
+  const uint32_t toplen = cl + (uint32_t)(32 - ptop);
+  if (fl) first(ctop, toplen); else emit(ctop, toplen);
+  const uint32_t S = T ^ (1u << ptop);  // lowest cells of the interior runs
+  if (S) {
+    const uint32_t t1 = T >> 1, t2 = T >> 2, t3 = T >> 3;
+    const uint32_t l1 = S & t1;
+    const uint32_t l2 = S & t2 & ~t1;
+    const uint32_t l3 = S & t3 & ~(t1 | t2);
+    sc.v12 += __popc(l1 & x) + (__popc(l2 & x) << 16);
+    sc.v3w1 += __popc(l3 & x) + (__popc(l1 & ~x) << 16);
+    sc.w23 += __popc(l2 & ~x) + (__popc(l3 & ~x) << 16);
+    uint32_t lg = S & ~(t1 | t2 | t3);
+    while (lg) {
+      const int q = __ffs(lg) - 1;
+      lg &= lg - 1;
+      const int nx = __ffs(T & ~lowmask(q + 1)) - 1;
+      emit((x >> q) & 1u, (uint32_t)(nx - q));
+    }
+  }
+  return (uint32_t)(__ffs(T) - 1) | ((x & 1u) << 28);
+}
+
+// Black-run scan of a full word (cells 31 .. 0), same contract as
+// scan_black(x, FULL, 31, 0, ...), with interior runs of length 1..3
+// counted by popcounts as in scan2_full.
+template <class E, class F>
+__device__ __forceinline__ uint32_t scanb_full(uint32_t x, uint32_t st, ShortCounts& sc,
+                                               E&& emit, F&& first) {
+  const uint32_t cl = st & ST_LEN;
+  if (x == FULL) return (cl + 32u) | (st & DG_EDGE);
+  const int zt = msb(~x);  // highest white cell
+  const uint32_t f = cl + (uint32_t)(31 - zt);
+  if (st & DG_EDGE)
+    first(f);
+  else if (f)
+    emit(f);
+  const uint32_t T = (x ^ (x << 1)) & 0xFFFFFFFEu;
+  const uint32_t Sb = T & x & lowmask(zt);  // lowest cells of interior black runs
+  if (Sb) {
+    const uint32_t t1 = T >> 1, t2 = T >> 2, t3 = T >> 3;
+    sc.d12 += __popc(Sb & t1) + (__popc(Sb & t2 & ~t1) << 16);
+    sc.d3 += __popc(Sb & t3 & ~(t1 | t2));
+    uint32_t lg = Sb & ~(t1 | t2 | t3);
+    while (lg) {
+      const int q = __ffs(lg) - 1;
+      lg &= lg - 1;
+      const int nx = __ffs(T & ~lowmask(q + 1)) - 1;
+      emit((uint32_t)(nx - q));
+    }
+  }
+  return (uint32_t)(__ffs(~x) - 1);
+}
+
+// Add a warp's short-line counters to the CTA's shared bins and clear them.
+__device__ __forceinline__ void flush_one(uint32_t x, uint32_t* dst, int lane) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+  if (lane == 0 && x) atomicAdd(dst, x);
+}
+__device__ __forceinline__ void flush_short(ShortCounts& sc, uint32_t* sh_hist, int lane) {
+  flush_one(sc.v12 & 0xFFFFu, sh_hist + HIST_VERT * HB + 1, lane);
+  flush_one(sc.v12 >> 16, sh_hist + HIST_VERT * HB + 2, lane);
+  flush_one(sc.v3w1 & 0xFFFFu, sh_hist + HIST_VERT * HB + 3, lane);
+  flush_one(sc.v3w1 >> 16, sh_hist + HIST_WHITE * HB + 1, lane);
+  flush_one(sc.w23 & 0xFFFFu, sh_hist + HIST_WHITE * HB + 2, lane);
+  flush_one(sc.w23 >> 16, sh_hist + HIST_WHITE * HB + 3, lane);
+  flush_one(sc.d12 & 0xFFFFu, sh_hist + HIST_DIAG * HB + 1, lane);
+  flush_one(sc.d12 >> 16, sh_hist + HIST_DIAG * HB + 2, lane);
+  flush_one(sc.d3, sh_hist + HIST_DIAG * HB + 3, lane);
+  sc = ShortCounts{0, 0, 0, 0, 0};
+}
+
 // ---------------------------------------------------------------- distances
 // FP32 margin of a pair: thr - d (L1, max) or thr - d^2 (L2), thr the scaled
 // radius (squared for L2).  Non-negative <=> recurrent in FP32.  Explicit
@@ -304,7 +411,7 @@ __host__ __device__ constexpr int tile_row_elems() {
 inline size_t tile_smem_bytes(int warps, int row_elems, int elem_bytes, int cols) {
   return (size_t)3 * HB * 4                                    // histograms
          + (size_t)warps * 32 * row_elems * elem_bytes          // row vectors
-         + (size_t)warps * 3 * cols * 32 * 4                    // per-warp column state
+         + (size_t)warps * 4 * cols * 32 * 4                    // per-warp column state
          + (size_t)(warps > 1 ? warps - 1 : 0) * RING * 64 * 4  // carry rings
          + (size_t)2 * warps * 4 + 16;
 }
@@ -326,10 +433,10 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
   T* rowbuf = reinterpret_cast<T*>(sh_hist + 3 * HB) + warp * 32 * RE;
   uint32_t* wstate =
       reinterpret_cast<uint32_t*>(reinterpret_cast<T*>(sh_hist + 3 * HB) + NW * 32 * RE);
-  uint32_t* Rw_s = wstate + warp * 3 * C * 32;   // recurrence words  [C][32]
+  uint32_t* Rw_s = wstate + warp * 4 * C * 32;   // recurrence words  [C][32]
   uint32_t* cst_s = Rw_s + C * 32;               // column run state  [C][32]
-  uint32_t* dU_s = cst_s + C * 32;               // diagonal up carry [C][32]
-  uint32_t* ring = wstate + NW * 3 * C * 32;
+  uint32_t* dU_s = cst_s + C * 32;               // diagonal up carry [2][C][32]
+  uint32_t* ring = wstate + NW * 4 * C * 32;
   volatile int* prod = reinterpret_cast<volatile int*>(ring + (NW > 1 ? NW - 1 : 0) * RING * 64);
   volatile int* cons = prod + NW;
   __shared__ int s_item;
@@ -415,6 +522,9 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
         cst_s[c * 32 + lane] = ST_FLAG;
         dU_s[c * 32 + lane] = 0;
       }
+      int bufo = 0;  // which half of dU_s holds the carries of the block below
+      ShortCounts sc{0, 0, 0, 0, 0};
+      int since_flush = 0;
       const float thr = Sp->thr;
       const float band = Sp->band;
       bool ok = true;
@@ -573,6 +683,10 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
 
         const int irow = r0 + lane;
         const bool row_valid = irow <= J1 - 2;
+        const int d = lane;
+        uint32_t* dU_old = dU_s + bufo * C * 32;
+        uint32_t* dU_new = dU_s + (bufo ^ 1) * C * 32;
+        uint32_t Dprev = 0;
 #pragma unroll 1
         for (int c = C - 1; c >= 0; --c) {
           const int col0 = jw0 + 32 * c;
@@ -582,12 +696,12 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           // ---- operator III, upper part of full column j (rows < j)
           {
             const int vt = j < 0 ? 0 : clamp32(j - r0);
-            if (vt > 0) {
-              cst_s[c * 32 + lane] = scan2(
-                  R, vt - 1, 0, cst_s[c * 32 + lane],
-                  [&](uint32_t col, uint32_t len) { hs.add2(col, len); },
-                  [&](uint32_t col, uint32_t len) { colend[j] = len | (col << 31); });
-            }
+            auto emitc = [&](uint32_t col, uint32_t len) { hs.add2(col, len); };
+            auto firstc = [&](uint32_t col, uint32_t len) { colend[j] = len | (col << 31); };
+            if (vt == 32)
+              cst_s[c * 32 + lane] = scan2_full(R, cst_s[c * 32 + lane], sc, emitc, firstc);
+            else if (vt > 0)
+              cst_s[c * 32 + lane] = scan2(R, vt - 1, 0, cst_s[c * 32 + lane], emitc, firstc);
           }
 
           // ---- operator III, lower part of full column irow = upper row irow
@@ -595,12 +709,14 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             const uint32_t RW = transpose32(R, lane);
             const int lo = irow + 1 - col0;  // first valid bit of the row
             if (lo <= 31 && !(rst & ST_DONE) && row_valid) {
-              const int lo_c = lo < 0 ? 0 : lo;
-              rst = scan2(
-                  RW, 31, lo_c, rst, [&](uint32_t col, uint32_t len) { hs.add2(col, len); },
-                  [&](uint32_t col, uint32_t len) {
-                    row_a[off + irow] = (uint16_t)((len << 1) | col);
-                  });
+              auto emitr = [&](uint32_t col, uint32_t len) { hs.add2(col, len); };
+              auto firstr = [&](uint32_t col, uint32_t len) {
+                row_a[off + irow] = (uint16_t)((len << 1) | col);
+              };
+              if (lo <= 0)
+                rst = scan2_full(RW, rst, sc, emitr, firstr);
+              else
+                rst = scan2(RW, 31, lo, rst, emitr, firstr);
               if (lo >= 0) {  // the row ends here, at column irow + 1
                 const uint32_t len = rst & ST_LEN, col = (rst >> 28) & 1u;
                 const uint32_t same = (rst >> 29) & 1u;
@@ -611,34 +727,44 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             }
           }
 
-          // ---- operator II, diagonal segments (lane d)
+          // ---- operator II: diagonal pieces (lane d)
           {
             const uint32_t rb = __brev(R);
-            const uint32_t Rr = __funnelshift_r(rb, rb, 31 - lane);
-            const uint32_t D = transpose32(Rr, lane);
-            const int d = lane;
-            // lower segment: bits d-1..0, diagonal k = col0 - r0 + d - 32,
-            // continues the upper segment of the block below.
-            const int klo = col0 - r0 + d - 32;
-            const uint32_t du = dU_s[c * 32 + lane];
-            uint32_t Lnext = du;
-            if (d > 0) {
-              Lnext = scan_black(
-                  D & segL, segL, d - 1, 0, du, [&](uint32_t len) { hs.add(HIST_DIAG, len); },
-                  [&](uint32_t len) {
-                    if (klo >= 1) dia_a[off + klo - 1] = (uint16_t)len;
-                  });
+            const uint32_t D = transpose32(__funnelshift_r(rb, rb, 31 - lane), lane);
+            const int k = col0 - r0 + d;  // diagonal of this sub-block's upper segment
+            auto emitd = [&](uint32_t len) { hs.add(HIST_DIAG, len); };
+            auto firstd = [&](uint32_t len) {
+              if (k >= 1) dia_a[off + k - 1] = (uint16_t)len;
+            };
+            if (c == C - 1) {
+              // upper segment only (bits 31..d), entering from the right
+              dU_new[c * 32 + lane] = scan_black(D & segU, segU, 31, d, dL, emitd, firstd);
+            } else {
+              // the lower segment of sub-block c+1 (bits d-1..0 of Dprev) and
+              // the upper segment of c (bits 31..d of D) are one diagonal;
+              // rotated by d its cells run from bit 31 down to bit 0
+              const uint32_t w = (Dprev & segL) | (D & segU);
+              const uint32_t y = __funnelshift_r(w, w, d);
+              dU_new[c * 32 + lane] = scanb_full(y, dU_old[(c + 1) * 32 + lane], sc, emitd, firstd);
             }
-            // upper segment: bits 31..d, diagonal k = col0 - r0 + d,
-            // continues the lower segment of the sub-block to the right.
-            const int kup = col0 - r0 + d;
-            dU_s[c * 32 + lane] = scan_black(
-                D & segU, segU, 31, d, dL, [&](uint32_t len) { hs.add(HIST_DIAG, len); },
-                [&](uint32_t len) {
-                  if (kup >= 1) dia_a[off + kup - 1] = (uint16_t)len;
-                });
-            dL = Lnext;
+            Dprev = D;
           }
+        }
+        {  // the lower segment of sub-block 0 (bits d-1..0) leaves to the left
+          const int k = jw0 - r0 + d - 32;
+          const uint32_t du = dU_old[lane];
+          dL = du;
+          if (d > 0)
+            dL = scan_black(
+                Dprev & segL, segL, d - 1, 0, du, [&](uint32_t len) { hs.add(HIST_DIAG, len); },
+                [&](uint32_t len) {
+                  if (k >= 1) dia_a[off + k - 1] = (uint16_t)len;
+                });
+        }
+        bufo ^= 1;
+        if (++since_flush == FLUSH_BLOCKS) {
+          flush_short(sc, sh_hist, lane);
+          since_flush = 0;
         }
 
         // ---- carries leaving to the left
@@ -682,11 +808,12 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
               else
                 hs.add2(col, len);
             }
-            const uint32_t du = dU_s[c * 32 + lane];  // diagonal k = j ends at (0, j)
+            const uint32_t du = dU_s[bufo * C * 32 + c * 32 + lane];  // k = j ends at (0, j)
             dia_z[off + j - 1] = (uint16_t)((du & ST_LEN) | ((du & DG_EDGE) ? 0x8000u : 0u));
           }
         }
       }
+      flush_short(sc, sh_hist, lane);
     }
     __syncthreads();
     if (s_abort && threadIdx.x == 0)
