@@ -179,6 +179,37 @@ void rqa_destroy(rqa_handle* h);
 const char* rqa_strerror(int status);
 const char* rqa_last_error(const rqa_handle* h);
 
+/* ---------------------------------------------------- without allocation
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot let the library allocate device memory -- programs that hand the
+ * whole GPU to their own memory pool, services that must keep a fixed device
+ * footprint from start-up, or code paths where cudaMalloc's implicit
+ * synchronisation of the device would stall unrelated streams.
+ *
+ * rqa_run_noalloc() computes the three histograms of one series exactly as
+ * rqa_run_device() does, but keeps every intermediate buffer in one static
+ * device array of RQA_NOALLOC_SCRATCH_BYTES that each GPU loading the library
+ * holds until the process exits; it calls no cudaMalloc/cudaFree.
+ *   settings    analysis parameters (validated as by rqa_create)
+ *   dev_series  n_points FP64 values in device memory, read on cuda_stream
+ *   dev_hist    device buffer of 3 * (n_vec + 1) uint64 that receives the
+ *               diagonal, vertical and white-vertical histograms, laid out
+ *               like rqa_histogram (kind * (n_vec + 1) + length)
+ *   cuda_stream cudaStream_t (NULL: legacy default stream); the call returns
+ *               after the work on it has finished
+ * Series of more than RQA_NOALLOC_MAX_N embedded vectors are rejected with
+ * RQA_ETOOBIG before anything is launched.  All calls share the one array:
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make it before
+ * any stream capture.  rqa_noalloc_last_error() describes the last failure
+ * of the calling thread. */
+#define RQA_NOALLOC_MAX_N ((int64_t)32768)
+#define RQA_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+int rqa_run_noalloc(const rqa_settings* settings, const double* dev_series,
+                    int64_t n_points, uint64_t* dev_hist, void* cuda_stream);
+const char* rqa_noalloc_last_error(void);
+
 /* ----------------------------------------------------------------- batched
  * Many independent series in one submission: the work of all series is one
  * queue of (series, strip) items processed by persistent CTAs, one launch
