@@ -131,6 +131,23 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def tile_traffic(n):
+    """DRAM bytes per tile-kernel launch from the committed ncu summary, or
+    None if the kernel source changed since the counters were taken or the
+    workload differs."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "tile_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_2402_16853_b300", "csrc", "rqa_tile.cuh")
+    try:
+        rec = json.load(open(prof))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except Exception:
+        return None
+    if rec.get("kernel_source_sha256_16") != sha or rec.get("scaled_to_n_vec") != n:
+        return None
+    return rec.get("tile_kernel_dram_bytes_per_launch")
+
+
 def cpu_baseline(series, params, stride: int, target_s: float = 15.0):
     """The FP64 oracle as it stands, on the host's cores, over every
     stride-th column and diagonal of the same workload."""
@@ -253,13 +270,7 @@ def run_mine(args):
     k_ms = float(np.mean(kernel_ms))
     achieved = pairs * ops_per_pair / (k_ms / 1e3) / 1e12
     peak = sms * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("tile_kernel_dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = tile_traffic(n)
 
     # ---- end to end through the C ABI with host buffers
     host = torch.tensor(s, dtype=torch.float64).pin_memory().numpy()
