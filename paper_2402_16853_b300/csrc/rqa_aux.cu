@@ -21,6 +21,7 @@ namespace rqa {
 // ----------------------------------------------------------------- prepare
 __global__ void prepare_kernel(SeriesDesc* __restrict__ sd) {
   SeriesDesc& S = sd[blockIdx.x];
+  if (S.n <= 0 || !S.s || !S.counters) return;  // nothing to prepare
   __shared__ double s_mn[32], s_mx[32];
   __shared__ int s_bad[32];
   double mn = INFINITY, mx = -INFINITY;
@@ -111,6 +112,7 @@ __global__ void prepare_kernel(SeriesDesc* __restrict__ sd) {
 // ------------------------------------------------------------------- embed
 __global__ void embed_kernel(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
+  if (S.n <= 0 || !S.xe || !S.s) return;
   const int64_t total = S.n * S.mp;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
@@ -160,6 +162,7 @@ __device__ __forceinline__ void emit2(BlockHist& h, const SeriesDesc& S, uint32_
 // end run for the line-of-identity join.
 __global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
+  if (S.n <= 0 || !S.hist) return;
   __shared__ uint32_t sh[3 * HB];
   BlockHist h{sh};
   h.init();
@@ -206,6 +209,7 @@ __global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd) {
 // all-black flag.
 __global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
+  if (S.n <= 0 || !S.hist) return;
   __shared__ uint32_t sh[3 * HB];
   BlockHist h{sh};
   h.init();
@@ -235,6 +239,7 @@ __global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd) {
 // upper row j (by symmetry).  The cell (j, j) is black iff w = 0.
 __global__ void join_loi_kernel(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
+  if (S.n <= 0 || !S.hist) return;
   __shared__ uint32_t sh[3 * HB];
   BlockHist h{sh};
   h.init();
@@ -260,6 +265,7 @@ __global__ void join_loi_kernel(SeriesDesc* __restrict__ sd) {
 // identity, one line of length n when w = 0.
 __global__ void diag_full_kernel(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
+  if (S.n <= 0 || !S.hist) return;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l <= S.n;
        l += (int64_t)gridDim.x * blockDim.x) {
     unsigned long long v = 2ull * S.hist[HIST_DIAG * (S.n + 1) + l];

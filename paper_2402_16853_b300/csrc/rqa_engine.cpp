@@ -223,6 +223,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     size_t o_hist, o_ends, o_cnt, o_desc, o_series, o_xe;
   };
   std::vector<P> plan(count);
+  std::vector<int> dev_idx(count, -1);  // device slot of each runnable series
+  int nrun = 0;
   using Key = std::tuple<int, int, int, int>;  // m, norm, f64, warps
   std::map<Key, int> cls_of;
   std::vector<Key> classes;
@@ -255,6 +257,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     P& p = plan[q];
     p.z = sizes_for(in[q].st, in[q].N, in[q].dev == nullptr);
     p.run = true;
+    dev_idx[q] = nrun++;
     const Key k{in[q].st.m, in[q].st.norm, p.z.f64 ? 1 : 0, p.z.tc.warps};
     auto it = cls_of.find(k);
     if (it == cls_of.end()) {
@@ -270,13 +273,17 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     total_items += p.z.nstrips;
   }
   const int ncls = static_cast<int>(classes.size());
-  if (ncls == 0) return RQA_OK;
+  if (ncls == 0) {  // nothing runnable: report the first validation failure
+    for (const auto& r : results)
+      if (r.status != RQA_OK) return r.status;
+    return RQA_OK;
+  }
 
   // ---- arena layout: [descs][items][queues | hists | counters | ends | boundary
   // descriptors (zeroed)][series copies | FP32 vectors]
   size_t off = 0;
   const size_t o_sd = off;
-  off += align256(sizeof(SeriesDesc) * count);
+  off += align256(sizeof(SeriesDesc) * nrun);
   const size_t o_items = off;
   off += align256(sizeof(Item) * static_cast<size_t>(std::max<int64_t>(total_items, 1)));
   const size_t o_zero = off;
@@ -321,7 +328,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   // host staging: [descs][items][hist readback][counter readback][series]
   size_t hoff = 0;
   const size_t h_sd = hoff;
-  hoff += align256(sizeof(SeriesDesc) * count);
+  hoff += align256(sizeof(SeriesDesc) * nrun);
   const size_t h_items = hoff;
   hoff += align256(sizeof(Item) * static_cast<size_t>(std::max<int64_t>(total_items, 1)));
   const size_t h_hist = hoff;
@@ -338,12 +345,12 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
 
   // ---- fill staging
   SeriesDesc* hsd = reinterpret_cast<SeriesDesc*>(host_ + h_sd);
-  std::memset(hsd, 0, sizeof(SeriesDesc) * count);
+  std::memset(hsd, 0, sizeof(SeriesDesc) * nrun);
   for (int q = 0; q < count; ++q) {
     const P& p = plan[q];
     if (!p.run) continue;
     const rqa_settings& s = in[q].st;
-    SeriesDesc& d = hsd[q];
+    SeriesDesc& d = hsd[dev_idx[q]];
     if (in[q].dev) {
       d.s = in[q].dev;
     } else {
@@ -382,7 +389,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       if (!p.run) continue;
       const int64_t sw = 32LL * p.z.tc.warps * p.z.tc.cols;
       for (int64_t Q = 0; Q < p.z.nstrips; ++Q)
-        per[p.cls].push_back({p.z.n - Q * sw, Item{q, static_cast<int32_t>(Q)}});
+        per[p.cls].push_back({p.z.n - Q * sw, Item{dev_idx[q], static_cast<int32_t>(Q)}});
     }
     int64_t pos = 0;
     for (int c = 0; c < ncls; ++c) {
@@ -433,10 +440,10 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
         (e = cudaMemcpyAsync(arena_ + o_series0, host_ + h_series, series_bytes,
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync(series)");
-    launch_prepare(d_sd, count, st);
+    launch_prepare(d_sd, nrun, st);
     ++launches;
     if (any_fp32) {
-      launch_embed(d_sd, count, max_n_mp, sms_, st);
+      launch_embed(d_sd, nrun, max_n_mp, sms_, st);
       ++launches;
     }
     if ((e = cudaEventRecord(ev_[1], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
@@ -470,13 +477,13 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       ctas_total += grid;
     }
     if ((e = cudaEventRecord(ev_[2], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-    launch_merges(d_sd, count, max_n, sms_, st);
+    launch_merges(d_sd, nrun, max_n, sms_, st);
     launches += 4;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "merge kernels launch");
     if ((e = cudaMemcpyAsync(host_ + h_hist, arena_ + o_hist0, hist_bytes + cnt_bytes,
                              cudaMemcpyDeviceToHost, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync(histograms)");
-    if ((e = cudaMemcpyAsync(host_ + h_sd, arena_ + o_sd, sizeof(SeriesDesc) * count,
+    if ((e = cudaMemcpyAsync(host_ + h_sd, arena_ + o_sd, sizeof(SeriesDesc) * nrun,
                              cudaMemcpyDeviceToHost, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync(series state)");
     if ((e = cudaEventRecord(ev_[3], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
@@ -531,7 +538,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       continue;
     }
     const uint64_t* cnt = reinterpret_cast<const uint64_t*>(host_ + h_cnt + (p.o_cnt - o_cnt0));
-    const SeriesDesc& d = hsd[q];
+    const SeriesDesc& d = hsd[dev_idx[q]];
     r.n = p.z.n;
     r.status = static_cast<int>(cnt[CNT_STATUS]);
     if (r.status == RQA_OK) {
@@ -560,7 +567,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     s.kernel_ms = tile_ms_;
     s.total_ms = total_ms_;
     s.h2d_bytes = static_cast<int64_t>((o_zero - o_sd) + series_bytes);
-    s.d2h_bytes = static_cast<int64_t>(hist_bytes + cnt_bytes + sizeof(SeriesDesc) * count);
+    s.d2h_bytes = static_cast<int64_t>(hist_bytes + cnt_bytes + sizeof(SeriesDesc) * nrun);
     s.launches = launches;
     s.ctas = static_cast<int32_t>(ctas_total);
   }

@@ -28,7 +28,7 @@ from scipy.signal import lfilter
 __all__ = [
     "logistic", "lorenz_x", "ar1", "sine_paper", "constant", "periodic",
     "dyadic", "zscore", "logistic_many", "lorenz_x_many", "ar1_many",
-    "SeriesSpec", "batch_specs", "make_series", "serve_stream",
+    "SeriesSpec", "draw_spec", "batch_specs", "make_series", "serve_stream",
     "WORKLOADS", "workload",
 ]
 
@@ -143,7 +143,8 @@ class SeriesSpec:
     w_min: int = 2
 
 
-def _draw_spec(rng, length: int) -> SeriesSpec:
+def draw_spec(rng, length: int) -> SeriesSpec:
+    """Parameters of one batched / served series (see batch_specs)."""
     kind = ("logistic", "lorenz", "ar1")[int(rng.integers(0, 3))]
     m = int(rng.integers(2, 9))
     tau = int(rng.integers(1, 5))
@@ -166,7 +167,7 @@ def batch_specs(count: int = 4096, seed: int = 1004, lo: int = 500,
     Theiler window 1, minimum line lengths 2."""
     rng = np.random.default_rng(seed)
     lengths = rng.integers(lo, hi + 1, size=count)
-    return [_draw_spec(rng, int(L)) for L in lengths]
+    return [draw_spec(rng, int(L)) for L in lengths]
 
 
 def make_series(specs, seed: int):
@@ -217,7 +218,7 @@ def serve_stream(rate: float = 200.0, duration: float = 60.0, seed: int = 1005,
         arrivals.append(t)
     k = len(arrivals)
     lengths = np.exp(rng.uniform(math.log(lo), math.log(hi), size=k)).astype(np.int64)
-    specs = [_draw_spec(rng, int(L)) for L in lengths]
+    specs = [draw_spec(rng, int(L)) for L in lengths]
     base_rng = np.random.default_rng(seed + 1)
     bases = {
         "logistic": logistic_many([hi] * pool, base_rng.uniform(3.6, 4.0, pool), base_rng),

@@ -1,0 +1,173 @@
+"""Batched and served RQA through the C ABI: every series of a batch, and
+every request of a served mix, must equal the FP64 oracle (and hence its own
+single-series run) exactly; admission must queue under a small memory
+budget and never exceed it; queued requests can be cancelled."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import assert_same_measures
+
+import paper_2402_16853_b300 as gp
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed(count, seed, lo=40, hi=3000):
+    rng = np.random.default_rng(seed)
+    specs = []
+    for q in range(count):
+        L = int(rng.integers(lo, hi))
+        sp = synth.draw_spec(rng, L)
+        specs.append(sp)
+    series, eps = synth.make_series(specs, seed)
+    settings = [gp.Settings(m=sp.m, tau=sp.tau, eps=e, norm=sp.norm, theiler=sp.theiler,
+                            l_min=sp.l_min, v_min=sp.v_min, w_min=sp.w_min)
+                for sp, e in zip(specs, eps)]
+    return settings, series
+
+
+def _oracle(st, s):
+    return oracle.rqa(s, oracle.Settings(m=st.m, tau=st.tau, eps=st.eps, norm=st.norm,
+                                         theiler=st.theiler, l_min=st.l_min, v_min=st.v_min,
+                                         w_min=st.w_min))
+
+
+def test_batch_equals_oracle_and_graph_replay():
+    settings, series = _mixed(40, 11)
+    # edge cases inside the batch: a single vector, a constant series, FP64 precision
+    settings.append(gp.Settings(m=3, tau=2, eps=0.2, norm=1, theiler=0))
+    series.append(np.array([0.1, 0.2, 0.3, 0.4, 0.5]))
+    settings.append(gp.Settings(m=2, tau=1, eps=0.1, norm=0, theiler=1))
+    series.append(np.full(700, 0.25))
+    settings.append(gp.Settings(m=4, tau=3, eps=0.4, norm=2, theiler=2, precision=gp.PREC_FP64))
+    series.append(synth.ar1(900, 5, 0.8))
+    b = gp.Batch()
+    res, st, rc = b.run(settings, series)
+    assert rc == 0 and all(x == 0 for x in st)
+    for q, (stg, s) in enumerate(zip(settings, series)):
+        want = _oracle(stg, s)
+        assert np.array_equal(b.histogram(q, 0), want["hd"]), q
+        assert np.array_equal(b.histogram(q, 1), want["hv"]), q
+        assert np.array_equal(b.histogram(q, 2), want["hw"]), q
+        assert_same_measures(res[q], want["measures"])
+    res2, st2, rc2 = b.run(settings, series)   # replays the captured graph
+    assert rc2 == 0
+    for m1, m2 in zip(res, res2):
+        assert_same_measures(m2, m1)
+
+
+def test_batch_failing_series_is_isolated():
+    settings, series = _mixed(8, 12)
+    bad = synth.ar1(500, 3, 0.9)
+    bad[17] = np.inf
+    settings.insert(3, gp.Settings(m=2, tau=1, eps=0.3, norm=1, theiler=1))
+    series.insert(3, bad)
+    settings.insert(5, gp.Settings(m=3, tau=4, eps=0.3, norm=1, theiler=1))
+    series.insert(5, np.zeros(5))   # too short for the embedding
+    b = gp.Batch()
+    res, st, rc = b.run(settings, series)
+    assert st[3] == 3 and st[5] == 2 and rc != 0
+    for q, (stg, s) in enumerate(zip(settings, series)):
+        if q in (3, 5):
+            assert res[q] is None
+            continue
+        assert_same_measures(res[q], _oracle(stg, s)["measures"])
+
+
+def test_served_results_equal_alone_and_in_the_mix():
+    settings, series = _mixed(60, 13, lo=100, hi=6000)
+    alone = []
+    for stg, s in zip(settings, series):
+        r = gp.RQA(stg)
+        alone.append(r.run(s))
+    srv = gp.Server(1 << 30, max_slots=16)
+    try:
+        _served_mix(srv, settings, series, alone)
+    finally:
+        srv.close()
+
+
+def _served_mix(srv, settings, series, alone):
+    tickets = []
+
+    def submitter(lo, hi):
+        for q in range(lo, hi):
+            tickets.append((q, srv.submit(settings[q], series[q])))
+            time.sleep(0.001)
+
+    th = [threading.Thread(target=submitter, args=(k * 20, (k + 1) * 20)) for k in range(3)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for q, t in tickets:
+        rc, m = srv.wait(t, 60_000)
+        assert rc == 0, (q, rc)
+        assert_same_measures(m, alone[q])
+    c = srv.counters()
+    assert c["completed"] == len(series) and c["bytes_in_use"] == 0 and c["epochs"] >= 1
+
+
+def test_admission_small_budget_never_overcommits():
+    settings, series = _mixed(30, 14, lo=2000, hi=4000)
+    srv = gp.Server(24 << 20, max_slots=4)   # 24 MiB: a few requests at a time
+    try:
+        _admission(srv, settings, series)
+    finally:
+        srv.close()
+
+
+def _admission(srv, settings, series):
+    peak = [0, 0]
+    stop = threading.Event()
+
+    def watch():
+        while not stop.is_set():
+            c = srv.counters()
+            peak[0] = max(peak[0], c["bytes_in_use"])
+            peak[1] = max(peak[1], c["in_flight"])
+            time.sleep(0.0005)
+
+    w = threading.Thread(target=watch)
+    w.start()
+    try:
+        ts = [srv.submit(stg, s) for stg, s in zip(settings, series)]
+        for t, stg, s in zip(ts, settings, series):
+            rc, m = srv.wait(t, 60_000)
+            assert rc == 0
+            assert_same_measures(m, _oracle(stg, s)["measures"])
+    finally:
+        stop.set()
+        w.join()
+    assert 0 < peak[0] <= 24 << 20 and 1 <= peak[1] <= 4
+
+
+def test_oversized_request_and_cancel():
+    srv = gp.Server(8 << 20, max_slots=1)
+    try:
+        _oversized_and_cancel(srv)
+    finally:
+        srv.close()
+
+
+def _oversized_and_cancel(srv):
+    big = synth.ar1(60000, 1, 0.9)
+    with pytest.raises(gp.RQAError) as ei:
+        srv.submit(gp.Settings(m=3, tau=1, eps=0.5, norm=1, theiler=1), big)
+    assert ei.value.status == 4   # RQA_ENOMEM: more than the budget allows
+    small = [synth.ar1(3000, k, 0.9) for k in range(6)]
+    st = gp.Settings(m=3, tau=1, eps=0.5, norm=1, theiler=1)
+    ts = [srv.submit(st, s) for s in small]
+    # the last ones are still queued behind a single slot: cancel one
+    rel = srv.release(ts[-1])
+    assert rel in (0, 7)
+    for t in ts[:-1]:
+        rc, m = srv.wait(t, 60_000)
+        assert rc == 0
+    if rel == 0:
+        assert srv.poll(ts[-1])[0] == 10   # forgotten

@@ -1,0 +1,114 @@
+"""Full-size checks in the launch configuration bench.py times.
+
+* Lorenz-x, N = 100,000 (n = 99,988, max norm, w = 5): all histograms and
+  measures bit-exact against the streaming FP64 oracle.
+* AR(1), N = 1,048,576 (n = 1,048,574, L2, w = 1): too large for the oracle,
+  so it is checked by properties that hold at any size and by sampled
+  decisions:
+  - the diagonal scan and the column / row scans see the same recurrence
+    points (sum l P_D(l) == sum l P_V(l)), and white lines cover the rest of
+    the n^2 cells;
+  - the FP32 + FP64-recheck path and the FP64-everywhere path give identical
+    histograms;
+  - 200,000 decisions R_ij, drawn uniformly, near the line of identity and
+    near the radius, equal the oracle's FP64 decisions one by one.
+* The paper's timing series (Sect. 8.2, sin over 1,000,001 points, m = 2,
+  tau = 2, eps = 1, no Theiler window): the line of identity is one line of
+  length n, and the diagonal histogram is otherwise even (both triangles).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import assert_same_measures
+
+import paper_2402_16853_b300 as gp
+
+pytestmark = pytest.mark.gpu
+
+
+def test_lorenz_n100k_bit_exact():
+    s, p = synth.workload("lorenz_n100k")
+    want = oracle.rqa(s, oracle.Settings(**p), mode="streaming")
+    r = gp.RQA(gp.Settings(**p))
+    meas = r.run(s)
+    hd, hv, hw = r.histograms()
+    assert np.array_equal(hd, want["hd"])
+    assert np.array_equal(hv, want["hv"])
+    assert np.array_equal(hw, want["hw"])
+    assert_same_measures(meas, want["measures"])
+
+
+@pytest.fixture(scope="module")
+def ar1_full():
+    s, p = synth.workload("ar1_n1m")
+    r = gp.RQA(gp.Settings(**p))
+    meas = r.run(s)
+    return s, p, r, meas, r.histograms(), r.stats()
+
+
+def test_ar1_n1m_invariants(ar1_full):
+    s, p, r, meas, (hd, hv, hw), st = ar1_full
+    n = len(s) - (p["m"] - 1) * p["tau"]
+    L = np.arange(n + 1, dtype=np.uint64)
+    rp_d = int((L * hd).sum())
+    rp_v = int((L * hv).sum())
+    assert rp_d == rp_v == meas["recurrence_points"]
+    assert int((L * hw).sum()) == n * n - rp_v
+    assert hd[0] == hv[0] == hw[0] == 0
+    assert int(hd.sum()) % 2 == 0           # w = 1: every line has a mirror image
+    assert st["exact"] == 1 and st["rechecks"] > 0
+
+
+def test_ar1_n1m_fp64_path_identical(ar1_full):
+    s, p, r, meas, (hd, hv, hw), st = ar1_full
+    r64 = gp.RQA(gp.Settings(**p, precision=gp.PREC_FP64))
+    m64 = r64.run(s)
+    h64 = r64.histograms()
+    assert np.array_equal(h64[0], hd) and np.array_equal(h64[1], hv)
+    assert np.array_equal(h64[2], hw)
+    assert_same_measures(m64, meas)
+
+
+def test_ar1_n1m_sampled_decisions(ar1_full):
+    s, p, r, meas, hists, st = ar1_full
+    n = len(s) - (p["m"] - 1) * p["tau"]
+    rng = np.random.default_rng(99)
+    i = rng.integers(0, n, 100_000)
+    j = rng.integers(0, n, 100_000)
+    k = rng.integers(0, 40, 50_000)            # near the line of identity
+    i2 = rng.integers(0, n - 40, 50_000)
+    i = np.concatenate([i, i2])
+    j = np.concatenate([j, i2 + k])
+    # pairs close to the radius: search a random pool for the smallest |d - eps|
+    pi = rng.integers(0, n, 2_000_000)
+    pj = rng.integers(0, n, 2_000_000)
+    x = np.stack([s[pi + q * p["tau"]] - s[pj + q * p["tau"]] for q in range(p["m"])])
+    d = np.sqrt((x * x).sum(axis=0))
+    near = np.argsort(np.abs(d - p["eps"]))[:50_000]
+    i = np.concatenate([i, pi[near]])
+    j = np.concatenate([j, pj[near]])
+    got = r.sample(i, j)
+    st_o = oracle.Settings(**p)
+    want = np.array([oracle.distance(s, a, b, p["m"], p["tau"], p["norm"]) <= p["eps"]
+                     and abs(a - b) >= p["theiler"] for a, b in zip(i, j)], dtype=np.uint8)
+    assert np.array_equal(got, want)
+    del st_o
+
+
+def test_paper_sine_series():
+    s = synth.sine_paper()
+    st = gp.Settings(m=2, tau=2, eps=1.0, norm=gp.NORM_L2, theiler=0)
+    r = gp.RQA(st)
+    meas = r.run(s)
+    hd, hv, hw = r.histograms()
+    n = len(s) - 2
+    assert meas["n_vec"] == n == 999_999
+    assert hd[n] == 1 and meas["l_max"] == n      # the line of identity (Table 3 reading)
+    off = hd.copy()
+    off[n] -= 1
+    assert np.all(off % 2 == 0)                   # the two triangles mirror each other
+    L = np.arange(n + 1, dtype=np.uint64)
+    assert int((L * hd).sum()) == int((L * hv).sum()) == meas["recurrence_points"]
+    assert int((L * hw).sum()) == n * n - meas["recurrence_points"]
