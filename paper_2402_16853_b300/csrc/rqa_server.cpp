@@ -4,14 +4,16 @@
 // Requests are copied at submission and queued in arrival order.  Worker
 // threads, each owning an engine with its own CUDA stream and device arena,
 // repeatedly admit the longest prefix of the queue whose device memory fits
-// in the worker's share of the budget (and the free slots), run it as one
-// launch epoch (all kernels of all admitted series in one submission), and
-// publish the results.  With two or more workers, an epoch formed from
+// in the worker's share of the budget (and the free slots) and whose work
+// stays below an epoch size, run it as one launch epoch (all kernels of all
+// admitted series in one submission), and publish the results.  With
+// several workers, an epoch formed from
 // requests that arrived while another epoch runs goes to the device at once
 // on its own stream, so work of different epochs overlaps.  Per-request
 // histograms and boundary state live in the epoch's device arena until the
 // epoch completes.
 #include <chrono>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -33,6 +35,7 @@ struct Request {
   rqa_settings st{};
   std::vector<double> series;
   size_t bytes = 0;
+  double cells = 0.0;  // n^2, the epoch-sizing estimate of its GPU work
   int status = RQA_PENDING;
   rqa_measures_t meas{};
   bool queued = true;
@@ -43,7 +46,11 @@ struct Request {
 struct rqa_server {
   size_t budget = 0;
   int32_t max_slots = 0;
-  int workers_n = 2;
+  int workers_n = 4;
+  // An epoch stops admitting once it holds this many matrix cells (about 10 ms
+  // of tile-kernel work), so epochs stay short and a request that arrives
+  // while one runs is picked up by the next free worker.
+  double epoch_cells = 1.5e10;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<std::shared_ptr<Request>> queue;
@@ -66,6 +73,7 @@ void rqa_server::worker(int idx) {
   for (;;) {
     std::vector<std::shared_ptr<Request>> epoch;
     size_t bytes = 0;
+    double cells = 0.0;
     {
       std::unique_lock<std::mutex> lk(mu);
       cv_work.wait(lk, [&] { return stop || !queue.empty(); });
@@ -76,6 +84,8 @@ void rqa_server::worker(int idx) {
         if (slots_used >= max_slots) break;
         if (bytes + r->bytes > share) break;
         if (in_use + r->bytes > budget) break;
+        if (!epoch.empty() && cells + r->cells > epoch_cells) break;
+        cells += r->cells;
         bytes += r->bytes;
         in_use += r->bytes;
         ++slots_used;
@@ -137,7 +147,15 @@ int rqa_server_create(size_t mem_budget_bytes, int32_t max_slots, rqa_server** o
   s->budget = mem_budget_bytes;
   s->max_slots = max_slots;
   s->device = dev;
-  s->workers_n = 2;
+  s->workers_n = 4;
+  if (const char* e = std::getenv("RQA_SERVE_WORKERS")) {  // tuning override
+    const int w = std::atoi(e);
+    if (w >= 1 && w <= 16) s->workers_n = w;
+  }
+  if (const char* e = std::getenv("RQA_SERVE_EPOCH_CELLS")) {
+    const double c = std::atof(e);
+    if (c > 0) s->epoch_cells = c;
+  }
   for (int w = 0; w < s->workers_n; ++w) s->threads.emplace_back(&rqa_server::worker, s, w);
   *out = s;
   return RQA_OK;
@@ -155,6 +173,7 @@ int rqa_submit(rqa_server* s, const rqa_settings* settings, const double* host_s
   auto r = std::make_shared<Request>();
   r->st = *settings;
   r->bytes = rqa::series_device_bytes(*settings, n);
+  r->cells = static_cast<double>(nv) * static_cast<double>(nv);
   if (r->bytes > s->budget / static_cast<size_t>(s->workers_n)) return RQA_ENOMEM;
   r->series.assign(host_series, host_series + n);
   {
