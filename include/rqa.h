@@ -210,6 +210,20 @@ int rqa_run_noalloc(const rqa_settings* settings, const double* dev_series,
                     int64_t n_points, uint64_t* dev_hist, void* cuda_stream);
 const char* rqa_noalloc_last_error(void);
 
+/* ------------------------------------------------------ recurrence plot
+ * The paper's RecurrencePlotComputation (Sect. 7.3, Table 2): a window of the
+ * recurrence matrix, rows [i0, i0 + rows) and columns [j0, j0 + cols), written
+ * bit-packed to host memory: plot row r occupies ceil(cols / 32) uint32
+ * words, bit b of word w is R(i0 + r, j0 + 32 w + b); cells outside the
+ * n x n matrix are 0.  The decisions are exactly those of rqa_run (FP32 with
+ * the FP64 recheck band, or FP64).  The buffer needs rows * ceil(cols/32) * 4
+ * bytes (at most 4 GiB).  rqa_plot_last_error() describes the last failure
+ * of the calling thread. */
+int rqa_recurrence_plot(const rqa_settings* settings, const double* host_series,
+                        int64_t n_points, int64_t i0, int64_t j0, int64_t rows,
+                        int64_t cols, uint32_t* out_bits);
+const char* rqa_plot_last_error(void);
+
 /* ----------------------------------------------------------------- batched
  * Many independent series in one submission: the work of all series is one
  * queue of (series, strip) items processed by persistent CTAs, one launch

@@ -323,6 +323,41 @@ __global__ void sample_kernel(const SeriesDesc* __restrict__ sd, const int64_t* 
   }
 }
 
+// -------------------------------------------------------- recurrence plot
+// One thread per 32-bit word of the bit-packed plot: word w of plot row r
+// holds R(i0 + r, j0 + 32 w + b) in bit b (0 outside the matrix).
+__global__ void plot_kernel(const SeriesDesc* __restrict__ sd, int64_t i0, int64_t j0,
+                            int64_t rows, int64_t cols, uint32_t* __restrict__ out, int f64) {
+  const SeriesDesc& S = sd[0];
+  const int64_t wpr = (cols + 31) / 32;
+  const int64_t total = rows * wpr;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = q / wpr, w = q - r * wpr;
+    const int64_t i = i0 + r;
+    uint32_t word = 0;
+    for (int b = 0; b < 32; ++b) {
+      const int64_t c = w * 32 + b, j = j0 + c;
+      if (c >= cols || i < 0 || j < 0 || i >= S.n || j >= S.n) continue;
+      bool rr;
+      if (S.norm == 1) rr = sample_one<1>(S, i, j, f64);
+      else if (S.norm == 2) rr = sample_one<2>(S, i, j, f64);
+      else rr = sample_one<0>(S, i, j, f64);
+      word |= (rr ? 1u : 0u) << b;
+    }
+    out[q] = word;
+  }
+}
+
+void launch_plot(const SeriesDesc* d_sd, int64_t i0, int64_t j0, int64_t rows, int64_t cols,
+                 uint32_t* out, int f64, int sms, cudaStream_t st) {
+  const int64_t total = rows * ((cols + 31) / 32);
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 16 * (int64_t)sms) blocks = 16 * (int64_t)sms;
+  if (blocks < 1) blocks = 1;
+  plot_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_sd, i0, j0, rows, cols, out, f64);
+}
+
 // ------------------------------------------------------------ host launch
 void launch_prepare(SeriesDesc* d_sd, int count, cudaStream_t st) {
   prepare_kernel<<<count, 256, 0, st>>>(d_sd);

@@ -22,6 +22,8 @@ TileFn tile_kernel_norm2(int m, int cols, bool f64);
 void launch_prepare(SeriesDesc* d_sd, int count, cudaStream_t st);
 void launch_embed(SeriesDesc* d_sd, int count, int64_t max_n_mp, int sms, cudaStream_t st);
 void launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, int sms, cudaStream_t st);
+void launch_plot(const SeriesDesc* d_sd, int64_t i0, int64_t j0, int64_t rows, int64_t cols,
+                 uint32_t* out, int f64, int sms, cudaStream_t st);
 void launch_sample(const SeriesDesc* d_sd, const int64_t* ii, const int64_t* jj, int64_t count,
                    uint8_t* out, int f64, cudaStream_t st);
 

@@ -123,6 +123,9 @@ def load(path: str = LIB_PATH):
         "rqa_release": (c.c_int, [vp, c.c_uint64]),
         "rqa_server_counters": (c.c_int, [vp] + [P(c.c_int64)] * 6),
         "rqa_server_destroy": (None, [vp]),
+        "rqa_recurrence_plot": (c.c_int, [P(_CSettings), P(c.c_double), c.c_int64, c.c_int64,
+                                          c.c_int64, c.c_int64, c.c_int64, P(c.c_uint32)]),
+        "rqa_plot_last_error": (c.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -349,3 +352,37 @@ class Server:
         load().rqa_server_counters(self._h, *[ctypes.byref(v) for v in vals])
         keys = ("admitted", "completed", "queued", "in_flight", "bytes_in_use", "epochs")
         return {k: v.value for k, v in zip(keys, vals)}
+
+
+def recurrence_plot(settings: Settings, series, i0: int = 0, j0: int = 0,
+                    rows: Optional[int] = None, cols: Optional[int] = None,
+                    packed: bool = False):
+    """A window of the recurrence matrix (the paper's RecurrencePlotComputation)
+    computed on the GPU.  Returns a (rows, cols) uint8 array of 0/1, or with
+    packed=True the raw (rows, ceil(cols/32)) uint32 words (bit b of word w is
+    column 32 w + b)."""
+    s = _f64(series)
+    n = len(s) - (settings.m - 1) * settings.tau
+    rows = n - i0 if rows is None else rows
+    cols = n - j0 if cols is None else cols
+    wpr = (cols + 31) // 32
+    out = np.zeros((max(rows, 0), wpr), dtype=np.uint32)
+    cs = _cs(settings)
+    rc = load().rqa_recurrence_plot(ctypes.byref(cs), s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    len(s), i0, j0, rows, cols,
+                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    if rc:
+        raise RQAError(rc, "rqa_recurrence_plot", load().rqa_plot_last_error().decode())
+    if packed:
+        return out
+    bits = np.unpackbits(out.view(np.uint8), axis=1, bitorder="little")
+    return bits[:, :cols]
+
+
+def write_pgm(path: str, plot) -> None:
+    """Write a 0/1 recurrence plot as a binary PGM image (recurrences black,
+    row 0 at the top), the headless form of the paper's plot image."""
+    img = np.where(np.asarray(plot, dtype=bool), 0, 255).astype(np.uint8)
+    with open(path, "wb") as f:
+        f.write(b"P5\n%d %d\n255\n" % (img.shape[1], img.shape[0]))
+        f.write(img.tobytes())
