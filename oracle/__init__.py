@@ -108,6 +108,20 @@ def _load():
             P(ctypes.c_double), ctypes.c_int64, P(_CSettings), ctypes.c_int32,
             ctypes.c_int64, P(ctypes.c_uint64), P(ctypes.c_uint64),
             P(ctypes.c_uint64), P(ctypes.c_uint64)]
+        lib.oracle_cross_distance.restype = ctypes.c_double
+        lib.oracle_cross_distance.argtypes = [P(ctypes.c_double), P(ctypes.c_double),
+                                              ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_int32]
+        lib.oracle_cross_histograms.restype = ctypes.c_uint64
+        lib.oracle_cross_histograms.argtypes = [
+            P(ctypes.c_double), ctypes.c_int64, P(ctypes.c_double), ctypes.c_int64,
+            P(_CSettings), ctypes.c_int32, P(ctypes.c_uint64), P(ctypes.c_uint64),
+            P(ctypes.c_uint64)]
+        lib.oracle_measures_rect.restype = None
+        lib.oracle_measures_rect.argtypes = [P(ctypes.c_uint64), P(ctypes.c_uint64),
+                                             P(ctypes.c_uint64), ctypes.c_int64,
+                                             ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
+                                             P(_CSettings), P(_CMeasures)]
         lib.oracle_measures.restype = None
         lib.oracle_measures.argtypes = [P(ctypes.c_uint64), P(ctypes.c_uint64),
                                         P(ctypes.c_uint64), ctypes.c_int64,
@@ -209,3 +223,26 @@ def rqa(series, st: Settings, mode: str = "auto", threads: int = 0):
         raise ValueError(mode)
     return {"hd": hd, "hv": hv, "hw": hw, "rp": rp, "n": n,
             "measures": measures(hd, hv, hw, n, rp, st)}
+
+
+def cross_distance(s1, s2, i: int, j: int, m: int, tau: int, norm: int) -> float:
+    a, b = _series(s1), _series(s2)
+    return float(_load().oracle_cross_distance(_dptr(a), _dptr(b), i, j, m, tau, norm))
+
+
+def cross_rqa(series1, series2, st: Settings, threads: int = 0):
+    """Cross recurrence: rows are the vectors of series1, columns those of
+    series2.  Returns the same dict as rqa() (n = rows, plus cols)."""
+    a, b = _series(series1), _series(series2)
+    n1 = nvec(len(a), st.m, st.tau)
+    n2 = nvec(len(b), st.m, st.tau)
+    L = max(n1, n2, 0)
+    hd, hv, hw = (np.zeros(L + 1, np.uint64) for _ in range(3))
+    cs = _cs(st)
+    rp = _load().oracle_cross_histograms(_dptr(a), len(a), _dptr(b), len(b), ctypes.byref(cs),
+                                         int(threads), _uptr(hd), _uptr(hv), _uptr(hw))
+    out = _CMeasures()
+    _load().oracle_measures_rect(_uptr(hd), _uptr(hv), _uptr(hw), L, n1, n2, int(rp),
+                                 ctypes.byref(cs), ctypes.byref(out))
+    return {"hd": hd, "hv": hv, "hw": hw, "rp": int(rp), "n": n1, "cols": n2,
+            "measures": {f: getattr(out, f) for f in MEASURE_FIELDS}}

@@ -256,6 +256,115 @@ uint64_t oracle_histograms_streaming(const double* s, int64_t N,
   return visited;
 }
 
+/* ------------------------------------------------------------------------
+ * Cross recurrence (the non-symmetric matrix of two series, Sect. 4.2:
+ * operator II's degree of parallelism 2N - 1 for non-symmetric matrices;
+ * Sect. 3.3 describes cross recurrence quantification).  Rows are the
+ * vectors x_i of series s1 (n1 of them), columns the vectors y_j of s2 (n2):
+ *   C_ij = 1 iff d(x_i, y_j) <= eps and |i - j| >= w,
+ * with the same distance and embedding readings R1-R3.  Lines are runs along
+ * the n1 + n2 - 1 diagonals (i, i + k), k in (-(n1-1), n2-1), and along the
+ * n2 columns of the n1 x n2 matrix (reading R4 on a rectangle).
+ * ------------------------------------------------------------------------ */
+double oracle_cross_distance(const double* s1, const double* s2, int64_t i, int64_t j,
+                             int32_t m, int32_t tau, int32_t norm) {
+  double acc = 0.0;
+  for (int32_t k = 0; k < m; ++k) {
+    double diff = s1[i + (int64_t)k * tau] - s2[j + (int64_t)k * tau];
+    if (norm == ORACLE_NORM_MAX) {
+      double ad = fabs(diff);
+      if (ad > acc) acc = ad;
+    } else if (norm == ORACLE_NORM_L1) {
+      acc = acc + fabs(diff);
+    } else {
+      acc = acc + diff * diff;
+    }
+  }
+  if (norm == ORACLE_NORM_L2) acc = sqrt(acc);
+  return acc;
+}
+
+static int cross_cell(const double* s1, const double* s2, int64_t i, int64_t j,
+                      const oracle_settings* st) {
+  int64_t gap = i > j ? i - j : j - i;
+  if (gap < (int64_t)st->theiler) return 0;
+  return oracle_cross_distance(s1, s2, i, j, st->m, st->tau, st->norm) <= st->eps;
+}
+
+/* Histograms (length max(n1, n2) + 1) of the n1 x n2 cross matrix, cells
+ * computed on the fly.  Returns the number of recurrence points. */
+uint64_t oracle_cross_histograms(const double* s1, int64_t N1, const double* s2,
+                                 int64_t N2, const oracle_settings* st,
+                                 int32_t threads, uint64_t* hd, uint64_t* hv,
+                                 uint64_t* hw) {
+  int64_t n1 = oracle_nvec(N1, st->m, st->tau);
+  int64_t n2 = oracle_nvec(N2, st->m, st->tau);
+  int64_t L = n1 > n2 ? n1 : n2;
+  memset(hd, 0, sizeof(uint64_t) * (size_t)(L + 1));
+  memset(hv, 0, sizeof(uint64_t) * (size_t)(L + 1));
+  memset(hw, 0, sizeof(uint64_t) * (size_t)(L + 1));
+  if (n1 <= 0 || n2 <= 0) return 0;
+  uint64_t ones = 0;
+#ifdef _OPENMP
+  if (threads > 0) omp_set_num_threads(threads);
+#else
+  (void)threads;
+#endif
+#pragma omp parallel reduction(+ : ones)
+  {
+    uint64_t* ld = (uint64_t*)calloc((size_t)(L + 1), sizeof(uint64_t));
+    uint64_t* lv = (uint64_t*)calloc((size_t)(L + 1), sizeof(uint64_t));
+    uint64_t* lw = (uint64_t*)calloc((size_t)(L + 1), sizeof(uint64_t));
+#pragma omp for schedule(dynamic, 1) nowait
+    for (int64_t k = -(n1 - 1); k <= n2 - 1; ++k) {
+      /* diagonal k: cells (i, i + k) inside the rectangle */
+      int64_t i0 = k >= 0 ? 0 : -k;
+      int prev = -1;
+      int64_t run = 0;
+      for (int64_t i = i0; i < n1 && i + k < n2; ++i) {
+        int v = cross_cell(s1, s2, i, i + k, st);
+        if (v == prev) {
+          run += 1;
+        } else {
+          if (prev >= 0) close_run(ld, NULL, prev, run);
+          prev = v;
+          run = 1;
+        }
+      }
+      if (prev >= 0) close_run(ld, NULL, prev, run);
+    }
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t j = 0; j < n2; ++j) {
+      int prev = -1;
+      int64_t run = 0;
+      for (int64_t i = 0; i < n1; ++i) {
+        int v = cross_cell(s1, s2, i, j, st);
+        ones += (uint64_t)v;
+        if (v == prev) {
+          run += 1;
+        } else {
+          if (prev >= 0) close_run(lv, lw, prev, run);
+          prev = v;
+          run = 1;
+        }
+      }
+      if (prev >= 0) close_run(lv, lw, prev, run);
+    }
+#pragma omp critical
+    {
+      for (int64_t l = 0; l <= L; ++l) {
+        hd[l] += ld[l];
+        hv[l] += lv[l];
+        hw[l] += lw[l];
+      }
+    }
+    free(ld);
+    free(lv);
+    free(lw);
+  }
+  return ones;
+}
+
 /* Sum over l >= lo of h[l] and of l * h[l], exactly in 64-bit integers. */
 static void hist_sums(const uint64_t* h, int64_t n, int64_t lo, uint64_t* s0,
                       uint64_t* s1) {
@@ -306,9 +415,23 @@ static double hist_entropy(const uint64_t* h, int64_t n, int64_t lo,
  *   LAM, TT, Vmax, V_entr: the same four with P_V and v_min
  *   W, Wmax, W_entr: the same with P_W and w_min (white vertical lines)
  * Every division is a plain IEEE division (0/0 gives NaN, x/0 gives inf). */
+void oracle_measures_rect(const uint64_t* hd, const uint64_t* hv,
+                          const uint64_t* hw, int64_t n, int64_t rows, int64_t cols,
+                          uint64_t rp, const oracle_settings* st,
+                          oracle_measures_t* out);
+
 void oracle_measures(const uint64_t* hd, const uint64_t* hv,
                      const uint64_t* hw, int64_t n, uint64_t rp,
                      const oracle_settings* st, oracle_measures_t* out) {
+  oracle_measures_rect(hd, hv, hw, n, n, n, rp, st, out);
+}
+
+/* The same measures for an n-by-m (cross) matrix: histograms of length
+ * n + 1 (n = the longer side), RR = RP / (rows * cols). */
+void oracle_measures_rect(const uint64_t* hd, const uint64_t* hv,
+                          const uint64_t* hw, int64_t n, int64_t rows, int64_t cols,
+                          uint64_t rp, const oracle_settings* st,
+                          oracle_measures_t* out) {
   uint64_t d0, d1, dall0, dall1, v0, v1, vall0, vall1, w0, w1;
   hist_sums(hd, n, st->l_min, &d0, &d1);
   hist_sums(hd, n, 1, &dall0, &dall1);
@@ -317,9 +440,9 @@ void oracle_measures(const uint64_t* hd, const uint64_t* hv,
   hist_sums(hw, n, st->w_min, &w0, &w1);
   (void)dall0;
   (void)vall0;
-  out->n_vec = n;
+  out->n_vec = rows;
   out->recurrence_points = (int64_t)rp;
-  out->rr = (double)rp / ((double)n * (double)n);
+  out->rr = (double)rp / ((double)rows * (double)cols);
   out->det = (double)d1 / (double)dall1;
   out->l = (double)d1 / (double)d0;
   out->l_max = hist_max(hd, n, st->l_min);
