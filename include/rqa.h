@@ -15,6 +15,11 @@
  *   4. the measures of Table 3 (RR, DET, L, Lmax, DIV, L_entr, LAM, TT, Vmax,
  *      V_entr) plus W, Wmax, W_entr for white vertical lines.
  * n = N - (m-1)*tau embedded vectors x_i = (s[i], s[i+tau], ..., s[i+(m-1)tau]).
+ * Cross recurrence (rqa_run_cross) compares the vectors x_i of one series
+ * with the vectors y_j of another (Sect. 3.3): the n1 x n2 matrix
+ * C_ij = [d(x_i, y_j) <= eps and |i-j| >= w], with lines along its
+ * n1 + n2 - 1 diagonals and down its n2 columns (Sect. 4.2, non-symmetric
+ * matrix).
  *
  * Results are exact: every recurrence decision equals the FP64 decision
  * d <= eps computed in the order
@@ -97,7 +102,7 @@ typedef struct {
  * the histograms of diagonal, vertical and white vertical line lengths over
  * the full matrix (line of identity included when w = 0) and RP the number
  * of recurrence points:
- *   rr = RP / (n*n)
+ *   rr = RP / (n*n)  (cross recurrence: RP / (n1*n2); n_vec = n1)
  *   det = sum_{l>=l_min} l P_D(l) / sum_{l>=1} l P_D(l)
  *   l = sum_{l>=l_min} l P_D(l) / sum_{l>=l_min} P_D(l)
  *   l_max = longest diagonal line >= l_min (0 if none), div = 1 / l_max
@@ -114,8 +119,9 @@ typedef struct {
 
 /* Diagnostics of the last run on a handle (not part of the result). */
 typedef struct {
-  int64_t n_vec;
-  int64_t pairs;          /* unique off-window pairs i < j, j - i >= max(w,1) */
+  int64_t n_vec;          /* rows: embedded vectors of the (first) series     */
+  int64_t pairs;          /* unique off-window pairs i < j, j - i >= max(w,1);
+                             cross recurrence: cells with |i - j| >= w        */
   int64_t rechecks;       /* pairs re-decided in FP64                         */
   double band;            /* recheck band used, in units of eps (eps^2 L2)    */
   double band_bound;      /* proven sufficient band, same units               */
@@ -130,7 +136,8 @@ typedef struct {
   int64_t h2d_bytes;      /* host-to-device bytes copied by the run           */
   int64_t d2h_bytes;      /* device-to-host bytes copied by the run           */
   int32_t launches;       /* kernels launched by the run                      */
-  int32_t reserved;
+  int32_t cross;          /* 1 if the run was a cross recurrence              */
+  int64_t n_cols;         /* columns: n_vec for RQA, n2 for cross recurrence  */
 } rqa_stats_t;
 
 typedef struct rqa_handle rqa_handle;
@@ -153,13 +160,26 @@ int rqa_run(rqa_handle* h, const double* host_series, int64_t n);
 int rqa_run_device(rqa_handle* h, const double* dev_series, int64_t n,
                    void* cuda_stream);
 
+/* Cross recurrence (Sect. 3.3; Sect. 4.2's non-symmetric matrix) of two host
+ * series: rows are the n1 = n_x - (m-1)*tau vectors of x, columns the
+ * n2 = n_y - (m-1)*tau vectors of y, cells with |i - j| < theiler are 0.
+ * The handle's settings apply to both series, which share one FP32
+ * centring and scaling so that the result is exact as for rqa_run.  After
+ * the call rqa_measures, rqa_histogram (entries l = 0..max(n1, n2)),
+ * rqa_stats and rqa_sample_decisions (i < n1, j < n2) describe the cross
+ * matrix.  The same series twice gives the result of rqa_run. */
+int rqa_run_cross(rqa_handle* h, const double* host_x, int64_t n_x,
+                  const double* host_y, int64_t n_y);
+/* The same with both series in device memory, ordered on cuda_stream. */
+int rqa_run_cross_device(rqa_handle* h, const double* dev_x, int64_t n_x,
+                         const double* dev_y, int64_t n_y, void* cuda_stream);
 /* Copy the measures of the last successful run. */
 int rqa_measures(const rqa_handle* h, rqa_measures_t* out);
 
 /* Copy a histogram of the last run: kind 0 = diagonal lines, 1 = vertical
  * lines, 2 = white vertical lines; entry l = number of lines of length l,
- * l = 0..n (entry 0 is always 0).  cap = capacity of `out` in entries;
- * *len receives n + 1.  RQA_EINVAL if cap < n + 1 (then *len still says how
+ * l = 0..n (entry 0 is always 0; cross recurrence: l = 0..max(n1, n2)).
+ * cap = capacity of `out` in entries; *len receives n + 1.  RQA_EINVAL if cap < n + 1 (then *len still says how
  * many entries are needed). */
 int rqa_histogram(const rqa_handle* h, int32_t kind, uint64_t* out,
                   int64_t cap, int64_t* len);
@@ -222,6 +242,12 @@ const char* rqa_noalloc_last_error(void);
 int rqa_recurrence_plot(const rqa_settings* settings, const double* host_series,
                         int64_t n_points, int64_t i0, int64_t j0, int64_t rows,
                         int64_t cols, uint32_t* out_bits);
+/* The same window of the cross-recurrence matrix of x (rows) and y
+ * (columns); cells outside the n1 x n2 matrix are 0. */
+int rqa_cross_recurrence_plot(const rqa_settings* settings, const double* host_x,
+                              int64_t n_x, const double* host_y, int64_t n_y,
+                              int64_t i0, int64_t j0, int64_t rows, int64_t cols,
+                              uint32_t* out_bits);
 const char* rqa_plot_last_error(void);
 
 /* ----------------------------------------------------------------- batched

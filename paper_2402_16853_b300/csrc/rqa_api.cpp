@@ -53,7 +53,7 @@ int find_device(int* dev, std::string* msg) {
 
 int copy_hist(const rqa::SeriesResult& r, int32_t kind, uint64_t* out, int64_t cap, int64_t* len) {
   if (kind < 0 || kind > 2) return RQA_EINVAL;
-  const int64_t need = r.n + 1;
+  const int64_t need = r.hl + 1;
   if (len) *len = need;
   if (!out || cap < need) return RQA_EINVAL;
   std::memcpy(out, r.hist.data() + kind * need, sizeof(uint64_t) * need);
@@ -103,11 +103,12 @@ int rqa_create(const rqa_settings* settings, rqa_handle** out) {
 }
 
 static int run_common(rqa_handle* h, const double* host, const double* dev, int64_t n,
-                      void* stream) {
+                      void* stream, bool cross = false, const double* host2 = nullptr,
+                      const double* dev2 = nullptr, int64_t n2 = 0) {
   if (!h) return RQA_EINVAL;
   h->have = false;
   h->err.clear();
-  if (!host && !dev) {
+  if ((!host && !dev) || (cross && !host2 && !dev2)) {
     h->err = "series pointer is NULL";
     return RQA_EINVAL;
   }
@@ -116,6 +117,10 @@ static int run_common(rqa_handle* h, const double* host, const double* dev, int6
   in[0].host = host;
   in[0].dev = dev;
   in[0].N = n;
+  in[0].cross = cross;
+  in[0].host2 = host2;
+  in[0].dev2 = dev2;
+  in[0].N2 = n2;
   std::vector<rqa::SeriesResult> res;
   int rc = h->eng->run(in, res, static_cast<cudaStream_t>(stream), false);
   if (rc != RQA_OK) {
@@ -133,6 +138,16 @@ int rqa_run(rqa_handle* h, const double* host_series, int64_t n) {
 
 int rqa_run_device(rqa_handle* h, const double* dev_series, int64_t n, void* cuda_stream) {
   return run_common(h, nullptr, dev_series, n, cuda_stream);
+}
+
+int rqa_run_cross(rqa_handle* h, const double* host_x, int64_t n_x, const double* host_y,
+                  int64_t n_y) {
+  return run_common(h, host_x, nullptr, n_x, nullptr, true, host_y, nullptr, n_y);
+}
+
+int rqa_run_cross_device(rqa_handle* h, const double* dev_x, int64_t n_x, const double* dev_y,
+                         int64_t n_y, void* cuda_stream) {
+  return run_common(h, nullptr, dev_x, n_x, cuda_stream, true, nullptr, dev_y, n_y);
 }
 
 int rqa_measures(const rqa_handle* h, rqa_measures_t* out) {

@@ -4,7 +4,8 @@
 //             FP32 recheck band;
 //   embed     time-delay embedding (Sect. 2, Sect. 7.2) into FP32 vectors;
 //   merge     join the boundary descriptors of the CTA strips along every
-//             row and every diagonal (the carryover buffers of Sect. 4.1);
+//             row and every diagonal (the carryover buffers of Sect. 4.1),
+//             for cross recurrence along the diagonals of the rectangle;
 //   finalize  join the runs of each full column at the line of identity and
 //             form the full diagonal histogram from the upper triangle;
 //   sample    individual decisions R_ij for spot checks.
@@ -26,8 +27,11 @@ __global__ void prepare_kernel(SeriesDesc* __restrict__ sd) {
   __shared__ int s_bad[32];
   double mn = INFINITY, mx = -INFINITY;
   int bad = 0;
-  for (int64_t i = threadIdx.x; i < S.N; i += blockDim.x) {
-    const double v = S.s[i];
+  // cross recurrence: both series share one centre and scale, so FP32
+  // differences of a row and a column vector are differences of the values
+  const int64_t total = S.cross ? S.N + S.N2 : S.N;
+  for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+    const double v = i < S.N ? S.s[i] : S.s2[i - S.N];
     if (!isfinite(v)) {
       bad = 1;
     } else {
@@ -110,18 +114,23 @@ __global__ void prepare_kernel(SeriesDesc* __restrict__ sd) {
 }
 
 // ------------------------------------------------------------------- embed
+// Rows' vectors into xe; for cross recurrence the columns' into xe2 after.
 __global__ void embed_kernel(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.xe || !S.s) return;
-  const int64_t total = S.n * S.mp;
+  const int64_t rows = S.n * S.mp;
+  const int64_t total = S.cross ? rows + S.n2 * S.mp : rows;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = q / S.mp;
-    const int k = (int)(q - i * S.mp);
+    const bool second = q >= rows;
+    const int64_t qq = second ? q - rows : q;
+    const double* src = second ? S.s2 : S.s;
+    const int64_t i = qq / S.mp;
+    const int k = (int)(qq - i * S.mp);
     float v = 0.f;
     if (k < S.m)
-      v = __double2float_rn(__dmul_rn(__dsub_rn(S.s[i + (int64_t)k * S.tau], S.center), S.scale));
-    S.xe[q] = v;
+      v = __double2float_rn(__dmul_rn(__dsub_rn(src[i + (int64_t)k * S.tau], S.center), S.scale));
+    (second ? S.xe2 : S.xe)[qq] = v;
   }
 }
 
@@ -135,8 +144,8 @@ struct BlockHist {
   __device__ void add(const SeriesDesc& S, int type, uint64_t len) {
     if (len < (uint64_t)HB && len > 0)
       atomicAdd(&sh[type * HB + len], 1u);
-    else if (len > 0 && len <= (uint64_t)S.n)
-      atomicAdd(&S.hist[type * (S.n + 1) + len], 1ull);
+    else if (len > 0 && len <= (uint64_t)S.hl)
+      atomicAdd(&S.hist[type * (S.hl + 1) + len], 1ull);
     else
       atomicExch(&S.counters[CNT_STATUS], STATUS_INTERNAL);
   }
@@ -144,7 +153,7 @@ struct BlockHist {
     __syncthreads();
     for (int q = threadIdx.x; q < 3 * HB; q += blockDim.x) {
       const uint32_t v = sh[q];
-      if (v) atomicAdd(&S.hist[(q / HB) * (S.n + 1) + (q % HB)], (unsigned long long)v);
+      if (v) atomicAdd(&S.hist[(q / HB) * (S.hl + 1) + (q % HB)], (unsigned long long)v);
     }
   }
 };
@@ -162,7 +171,7 @@ __device__ __forceinline__ void emit2(BlockHist& h, const SeriesDesc& S, uint32_
 // end run for the line-of-identity join.
 __global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
-  if (S.n <= 0 || !S.hist) return;
+  if (S.n <= 0 || !S.hist || S.cross) return;
   __shared__ uint32_t sh[3 * HB];
   BlockHist h{sh};
   h.init();
@@ -209,7 +218,7 @@ __global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd) {
 // all-black flag.
 __global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
-  if (S.n <= 0 || !S.hist) return;
+  if (S.n <= 0 || !S.hist || S.cross) return;
   __shared__ uint32_t sh[3 * HB];
   BlockHist h{sh};
   h.init();
@@ -234,12 +243,50 @@ __global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd) {
   h.flush(S);
 }
 
+// ------------------------------------------------ merge: cross diagonals
+// Cross recurrence: diagonal k (cells (i, i+k), -(n1-1) <= k <= n2-1) runs
+// from its bottom-right end, column min(n2-1, n1-1+k), to its top-left end,
+// column max(0, k), through strips Qa .. Qz (strip Q covers columns
+// [n2 - (Q+1) sw, n2 - Q sw)).  The descriptors mean what they mean for
+// RQA; runs touching the matrix border were closed in the tile kernel or
+// are closed here at the diagonal's ends.
+__global__ void merge_cross_diags_kernel(SeriesDesc* __restrict__ sd) {
+  const SeriesDesc& S = sd[blockIdx.y];
+  if (S.n <= 0 || !S.hist || !S.cross) return;
+  __shared__ uint32_t sh[3 * HB];
+  BlockHist h{sh};
+  h.init();
+  const int64_t n1 = S.n, n2 = S.n2, sw = S.sw, nd = cross_strip_diags(n1, sw);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n1 + n2 - 1;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = t - (n1 - 1);
+    const int64_t jlo = k > 0 ? k : 0;
+    const int64_t jhi = n1 - 1 + k < n2 - 1 ? n1 - 1 + k : n2 - 1;
+    const int64_t qa = (n2 - 1 - jhi) / sw, qz = (n2 - 1 - jlo) / sw;
+    uint64_t L = 0;
+    for (int64_t Q = qa; Q <= qz; ++Q) {
+      const int64_t klo = n2 - (Q + 1) * sw - (n1 - 1);
+      const int64_t o = Q * nd + (k - klo);
+      const uint32_t z = S.dia_z[o];
+      if (z & 0x8000u) {
+        L += (z & 0x7FFFu);
+      } else {
+        const uint64_t first = L + S.dia_a[o];
+        if (first) h.add(S, HIST_DIAG, first);
+        L = z & 0x7FFFu;
+      }
+    }
+    if (L) h.add(S, HIST_DIAG, L);
+  }
+  h.flush(S);
+}
+
 // ----------------------------------------------------------------- finalize
 // Full column j = upper column j (rows < j), the line-of-identity cell, and
 // upper row j (by symmetry).  The cell (j, j) is black iff w = 0.
 __global__ void join_loi_kernel(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
-  if (S.n <= 0 || !S.hist) return;
+  if (S.n <= 0 || !S.hist || S.cross) return;
   __shared__ uint32_t sh[3 * HB];
   BlockHist h{sh};
   h.init();
@@ -265,7 +312,7 @@ __global__ void join_loi_kernel(SeriesDesc* __restrict__ sd) {
 // identity, one line of length n when w = 0.
 __global__ void diag_full_kernel(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
-  if (S.n <= 0 || !S.hist) return;
+  if (S.n <= 0 || !S.hist || S.cross) return;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l <= S.n;
        l += (int64_t)gridDim.x * blockDim.x) {
     unsigned long long v = 2ull * S.hist[HIST_DIAG * (S.n + 1) + l];
@@ -275,34 +322,38 @@ __global__ void diag_full_kernel(SeriesDesc* __restrict__ sd) {
 }
 
 // ------------------------------------------------------------------ sample
+// R_ij with the tile kernel's decision code: row vector i (of s), column
+// vector j (of s2 for cross recurrence; RQA takes the pair as i < j).
 template <int NORM>
 __device__ bool sample_one(const SeriesDesc& S, int64_t i, int64_t j, bool f64) {
-  if (i > j) {
+  if (!S.cross && i > j) {
     const int64_t t = i;
     i = j;
     j = t;
   }
-  if (j - i < S.w) return false;
-  if (f64) return exact_decision<NORM>(S.s, i, j, S.m, S.tau, S.eps);
+  if ((i > j ? i - j : j - i) < S.w) return false;
+  const double* s2 = S.cross ? S.s2 : S.s;
+  const float* xe2 = S.cross ? S.xe2 : S.xe;
+  if (f64) return exact_decision2<NORM>(S.s, s2, i, j, S.m, S.tau, S.eps);
   // FP32 margin in the tile kernel's order (row vector i, column vector j)
   float acc;
   if (NORM == 1) {
     acc = S.thr;
     for (int k = 0; k < S.m; ++k) {
-      const float d = __fsub_rn(S.xe[i * S.mp + k], S.xe[j * S.mp + k]);
+      const float d = __fsub_rn(S.xe[i * S.mp + k], xe2[j * S.mp + k]);
       acc = __fmaf_rn(-d, d, acc);
     }
   } else if (NORM == 2) {
     acc = S.thr;
     for (int k = 0; k < S.m; ++k)
-      acc = __fsub_rn(acc, fabsf(__fsub_rn(S.xe[i * S.mp + k], S.xe[j * S.mp + k])));
+      acc = __fsub_rn(acc, fabsf(__fsub_rn(S.xe[i * S.mp + k], xe2[j * S.mp + k])));
   } else {
     float mx = 0.f;
     for (int k = 0; k < S.m; ++k)
-      mx = fmaxf(mx, fabsf(__fsub_rn(S.xe[i * S.mp + k], S.xe[j * S.mp + k])));
+      mx = fmaxf(mx, fabsf(__fsub_rn(S.xe[i * S.mp + k], xe2[j * S.mp + k])));
     acc = __fsub_rn(S.thr, mx);
   }
-  if (fabsf(acc) <= S.band) return exact_decision<NORM>(S.s, i, j, S.m, S.tau, S.eps);
+  if (fabsf(acc) <= S.band) return exact_decision2<NORM>(S.s, s2, i, j, S.m, S.tau, S.eps);
   return !(__float_as_uint(acc) >> 31);
 }
 
@@ -314,7 +365,7 @@ __global__ void sample_kernel(const SeriesDesc* __restrict__ sd, const int64_t* 
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = ii[q], j = jj[q];
     bool r = false;
-    if (i >= 0 && j >= 0 && i < S.n && j < S.n) {
+    if (i >= 0 && j >= 0 && i < S.n && j < S.n2) {
       if (S.norm == 1) r = sample_one<1>(S, i, j, f64);
       else if (S.norm == 2) r = sample_one<2>(S, i, j, f64);
       else r = sample_one<0>(S, i, j, f64);
@@ -338,7 +389,7 @@ __global__ void plot_kernel(const SeriesDesc* __restrict__ sd, int64_t i0, int64
     uint32_t word = 0;
     for (int b = 0; b < 32; ++b) {
       const int64_t c = w * 32 + b, j = j0 + c;
-      if (c >= cols || i < 0 || j < 0 || i >= S.n || j >= S.n) continue;
+      if (c >= cols || i < 0 || j < 0 || i >= S.n || j >= S.n2) continue;
       bool rr;
       if (S.norm == 1) rr = sample_one<1>(S, i, j, f64);
       else if (S.norm == 2) rr = sample_one<2>(S, i, j, f64);
@@ -368,14 +419,24 @@ void launch_embed(SeriesDesc* d_sd, int count, int64_t max_n_mp, int sms, cudaSt
   if (blocks < 1) blocks = 1;
   embed_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
 }
-void launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, int sms, cudaStream_t st) {
+int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cross, int sms,
+                  cudaStream_t st) {
   int64_t blocks = (max_n + 255) / 256;
   if (blocks > 4 * sms) blocks = 4 * sms;
   if (blocks < 1) blocks = 1;
-  merge_rows_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
-  merge_diags_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
-  join_loi_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
-  diag_full_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+  int launched = 0;
+  if (sym) {
+    merge_rows_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+    merge_diags_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+    join_loi_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+    diag_full_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+    launched += 4;
+  }
+  if (cross) {
+    merge_cross_diags_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+    launched += 1;
+  }
+  return launched;
 }
 void launch_sample(const SeriesDesc* d_sd, const int64_t* ii, const int64_t* jj, int64_t count,
                    uint8_t* out, int f64, cudaStream_t st) {

@@ -28,29 +28,54 @@ int64_t pair_count(int64_t n, int w) {
   return cnt * (cnt + 1) / 2;
 }
 
+// Cells of the n1 x n2 cross matrix outside the Theiler window |i - j| < w.
+int64_t cross_cell_count(int64_t n1, int64_t n2, int64_t w) {
+  int64_t cells = n1 * n2;
+  for (int64_t k = -(w - 1); k <= w - 1; ++k) {  // diagonal k: cells (i, i + k)
+    const int64_t lo = k < 0 ? -k : 0;
+    const int64_t hi = std::min(n1, n2 - k);
+    if (hi > lo) cells -= hi - lo;
+  }
+  return cells;
+}
+
 struct Sizes {
-  int64_t n = 0, nstrips = 0, ndesc = 0;
+  int64_t n = 0, n2 = 0, hl = 0, nstrips = 0, ndesc = 0;
   int mp = 0;
   TileConfig tc{1, 4};
-  bool f64 = false;
-  size_t hist = 0, ends = 0, cnt = 0, desc = 0, series = 0, xe = 0;
+  bool f64 = false, cross = false;
+  size_t hist = 0, ends = 0, cnt = 0, desc = 0, series = 0, series2 = 0, xe = 0, xe2 = 0;
 };
 
-Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series) {
+// Device buffers of one series (RQA) or one pair of series (cross
+// recurrence: rows from the N values, columns from the N2 values).
+Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross = false,
+                int64_t N2 = 0, bool copy_series2 = false) {
   Sizes z;
   z.n = nvec_of(st, N);
+  z.cross = cross;
+  z.n2 = cross ? nvec_of(st, N2) : z.n;
+  z.hl = std::max(z.n, z.n2);
   z.f64 = st.precision == RQA_PREC_FP64;
   z.mp = z.f64 ? 0 : ((st.m + 3) / 4) * 4;
-  z.tc = choose_tile(z.n, st.m, st.norm);
+  z.tc = choose_tile(z.n2, st.m, st.norm);
   const int64_t sw = 32LL * z.tc.warps * z.tc.cols;
-  z.nstrips = num_strips(z.n, sw);
-  z.ndesc = strip_offset(z.n, sw, z.nstrips);
-  z.hist = align256(sizeof(uint64_t) * 3 * static_cast<size_t>(z.n + 1));
-  z.ends = align256(sizeof(uint32_t) * 2 * static_cast<size_t>(z.n));
+  if (cross) {
+    z.nstrips = cross_num_strips(z.n2, sw);
+    z.ndesc = z.nstrips * cross_strip_diags(z.n, sw);
+  } else {
+    z.nstrips = num_strips(z.n, sw);
+    z.ndesc = strip_offset(z.n, sw, z.nstrips);
+  }
+  z.hist = align256(sizeof(uint64_t) * 3 * static_cast<size_t>(z.hl + 1));
+  z.ends = cross ? 0 : align256(sizeof(uint32_t) * 2 * static_cast<size_t>(z.n));
   z.cnt = align256(sizeof(uint64_t) * CNT_WORDS);
-  z.desc = 4 * align256(sizeof(uint16_t) * static_cast<size_t>(z.ndesc));
+  // RQA: row_a, row_z, dia_a, dia_z; cross recurrence: dia_a, dia_z
+  z.desc = (cross ? 2 : 4) * align256(sizeof(uint16_t) * static_cast<size_t>(z.ndesc));
   z.series = copy_series ? align256(sizeof(double) * static_cast<size_t>(N)) : 0;
+  z.series2 = cross && copy_series2 ? align256(sizeof(double) * static_cast<size_t>(N2)) : 0;
   z.xe = align256(sizeof(float) * static_cast<size_t>(z.n) * z.mp);
+  z.xe2 = cross ? align256(sizeof(float) * static_cast<size_t>(z.n2) * z.mp) : 0;
   return z;
 }
 
@@ -220,16 +245,16 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     Sizes z;
     int cls = -1;
     bool run = false;
-    size_t o_hist, o_ends, o_cnt, o_desc, o_series, o_xe;
+    size_t o_hist, o_ends, o_cnt, o_desc, o_series, o_series2, o_xe, o_xe2;
   };
   std::vector<P> plan(count);
   std::vector<int> dev_idx(count, -1);  // device slot of each runnable series
   int nrun = 0;
-  using Key = std::tuple<int, int, int, int>;  // m, norm, f64, warps
+  using Key = std::tuple<int, int, int, int, int>;  // m, norm, f64, warps, cross
   std::map<Key, int> cls_of;
   std::vector<Key> classes;
   int64_t max_n = 0, max_n_mp = 0, total_items = 0;
-  bool any_fp32 = false;
+  bool any_fp32 = false, any_sym = false, any_cross = false;
   for (int q = 0; q < count; ++q) {
     std::string msg;
     int s = validate_settings(&in[q].st, &msg);
@@ -249,26 +274,40 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       s = RQA_ETOOBIG;
       msg = "more than RQA_MAX_N embedded vectors";
     }
+    if (s == RQA_OK && in[q].cross) {
+      if (!in[q].host2 && !in[q].dev2) {
+        s = RQA_EINVAL;
+        msg = "second series pointer is NULL";
+      } else if (in[q].N2 < 1 || nvec_of(in[q].st, in[q].N2) < 1) {
+        s = RQA_ESHORT;
+        msg = "second series shorter than the embedding window (m-1)*tau + 1";
+      } else if (nvec_of(in[q].st, in[q].N2) > RQA_MAX_N) {
+        s = RQA_ETOOBIG;
+        msg = "more than RQA_MAX_N embedded vectors in the second series";
+      }
+    }
     if (s != RQA_OK) {
       results[q].status = s;
       if (count == 1) return fail(s, msg);
       continue;
     }
     P& p = plan[q];
-    p.z = sizes_for(in[q].st, in[q].N, in[q].dev == nullptr);
+    p.z = sizes_for(in[q].st, in[q].N, in[q].dev == nullptr, in[q].cross, in[q].N2,
+                    in[q].dev2 == nullptr);
     p.run = true;
     dev_idx[q] = nrun++;
-    const Key k{in[q].st.m, in[q].st.norm, p.z.f64 ? 1 : 0, p.z.tc.warps};
+    (p.z.cross ? any_cross : any_sym) = true;
+    const Key k{in[q].st.m, in[q].st.norm, p.z.f64 ? 1 : 0, p.z.tc.warps, p.z.cross ? 1 : 0};
     auto it = cls_of.find(k);
     if (it == cls_of.end()) {
       it = cls_of.emplace(k, static_cast<int>(classes.size())).first;
       classes.push_back(k);
     }
     p.cls = it->second;
-    max_n = std::max(max_n, p.z.n);
+    max_n = std::max(max_n, p.z.cross ? p.z.n + p.z.n2 : p.z.n);
     if (!p.z.f64) {
       any_fp32 = true;
-      max_n_mp = std::max(max_n_mp, p.z.n * p.z.mp);
+      max_n_mp = std::max(max_n_mp, (p.z.n + (p.z.cross ? p.z.n2 : 0)) * p.z.mp);
     }
     total_items += p.z.nstrips;
   }
@@ -316,12 +355,16 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     if (p.run) {
       p.o_series = off;
       off += p.z.series;
+      p.o_series2 = off;
+      off += p.z.series2;
     }
   const size_t series_bytes = off - o_series0;
   for (auto& p : plan)
     if (p.run) {
       p.o_xe = off;
       off += p.z.xe;
+      p.o_xe2 = off;
+      off += p.z.xe2;
     }
   const size_t arena_bytes = off;
 
@@ -361,22 +404,44 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     d.xe = p.z.f64 ? nullptr : reinterpret_cast<float*>(arena_ + p.o_xe);
     d.N = in[q].N;
     d.n = p.z.n;
+    desc_set_symmetric(d);
+    if (p.z.cross) {
+      if (in[q].dev2) {
+        d.s2 = in[q].dev2;
+      } else {
+        d.s2 = reinterpret_cast<const double*>(arena_ + p.o_series2);
+        std::memcpy(host_ + h_series + (p.o_series2 - o_series0), in[q].host2,
+                    sizeof(double) * static_cast<size_t>(in[q].N2));
+      }
+      d.xe2 = p.z.f64 ? nullptr : reinterpret_cast<float*>(arena_ + p.o_xe2);
+      d.N2 = in[q].N2;
+      d.n2 = p.z.n2;
+      d.hl = p.z.hl;
+      d.cross = 1;
+    }
     d.m = s.m;
     d.tau = s.tau;
     d.norm = s.norm;
-    d.w = s.theiler;
+    // a window of hl or more removes every cell, as any wider one does
+    d.w = static_cast<int32_t>(std::min<int64_t>(s.theiler, p.z.hl));
     d.mp = p.z.mp;
     d.sw = 32 * p.z.tc.warps * p.z.tc.cols;
     d.eps = s.eps;
     d.band_override = s.band_override;
     d.hist = reinterpret_cast<unsigned long long*>(arena_ + p.o_hist);
-    const size_t dbytes = p.z.desc / 4;
-    d.row_a = reinterpret_cast<uint16_t*>(arena_ + p.o_desc);
-    d.row_z = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + dbytes);
-    d.dia_a = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + 2 * dbytes);
-    d.dia_z = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + 3 * dbytes);
-    d.colend = reinterpret_cast<uint32_t*>(arena_ + p.o_ends);
-    d.rowend = d.colend + p.z.n;
+    if (p.z.cross) {
+      const size_t dbytes = p.z.desc / 2;
+      d.dia_a = reinterpret_cast<uint16_t*>(arena_ + p.o_desc);
+      d.dia_z = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + dbytes);
+    } else {
+      const size_t dbytes = p.z.desc / 4;
+      d.row_a = reinterpret_cast<uint16_t*>(arena_ + p.o_desc);
+      d.row_z = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + dbytes);
+      d.dia_a = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + 2 * dbytes);
+      d.dia_z = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + 3 * dbytes);
+      d.colend = reinterpret_cast<uint32_t*>(arena_ + p.o_ends);
+      d.rowend = d.colend + p.z.n;
+    }
     d.counters = reinterpret_cast<unsigned long long*>(arena_ + p.o_cnt);
   }
   // work items per class, longest strips first
@@ -388,8 +453,9 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       const P& p = plan[q];
       if (!p.run) continue;
       const int64_t sw = 32LL * p.z.tc.warps * p.z.tc.cols;
-      for (int64_t Q = 0; Q < p.z.nstrips; ++Q)
-        per[p.cls].push_back({p.z.n - Q * sw, Item{dev_idx[q], static_cast<int32_t>(Q)}});
+      for (int64_t Q = 0; Q < p.z.nstrips; ++Q)  // strip height: the rows it spans
+        per[p.cls].push_back({p.z.cross ? p.z.n : p.z.n - Q * sw,
+                              Item{dev_idx[q], static_cast<int32_t>(Q)}});
     }
     int64_t pos = 0;
     for (int c = 0; c < ncls; ++c) {
@@ -420,6 +486,9 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       key.push_back(in[q].st.norm);
       key.push_back(in[q].st.precision);
       key.push_back(in[q].st.tau);
+      key.push_back(in[q].cross ? 1 : 0);
+      key.push_back(in[q].N2);
+      key.push_back(reinterpret_cast<int64_t>(in[q].dev2));
     }
   }
   const bool replay = use_graph && graph_ && key == graph_key_;
@@ -451,7 +520,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       const int m = std::get<0>(classes[c]), norm = std::get<1>(classes[c]);
       const bool f64 = std::get<2>(classes[c]) != 0;
       const int warps = std::get<3>(classes[c]);
-      TileFn fn = tile_kernel_for(m, norm, 4, f64);
+      const bool cross = std::get<4>(classes[c]) != 0;
+      TileFn fn = tile_kernel_for(m, norm, 4, f64, cross);
       if (!fn) return fail(RQA_EINVAL, "no tile kernel for this (m, norm)");
       const size_t smem = tile_smem_for(m, norm, f64, warps, 4);
       if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
@@ -477,8 +547,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       ctas_total += grid;
     }
     if ((e = cudaEventRecord(ev_[2], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-    launch_merges(d_sd, nrun, max_n, sms_, st);
-    launches += 4;
+    launches += launch_merges(d_sd, nrun, max_n, any_sym, any_cross, sms_, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "merge kernels launch");
     if ((e = cudaMemcpyAsync(host_ + h_hist, arena_ + o_hist0, hist_bytes + cnt_bytes,
                              cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -540,13 +609,16 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     const uint64_t* cnt = reinterpret_cast<const uint64_t*>(host_ + h_cnt + (p.o_cnt - o_cnt0));
     const SeriesDesc& d = hsd[dev_idx[q]];
     r.n = p.z.n;
+    r.n2 = p.z.n2;
+    r.hl = p.z.hl;
     r.status = static_cast<int>(cnt[CNT_STATUS]);
     if (r.status == RQA_OK) {
       const uint64_t* h = reinterpret_cast<const uint64_t*>(host_ + h_hist + (p.o_hist - o_hist0));
-      r.hist.assign(h, h + 3 * (p.z.n + 1));
-      measures_from_histograms(r.hist.data(), r.hist.data() + (p.z.n + 1),
-                               r.hist.data() + 2 * (p.z.n + 1), p.z.n, in[q].st.l_min,
-                               in[q].st.v_min, in[q].st.w_min, &r.meas);
+      const int64_t L1 = p.z.hl + 1;
+      r.hist.assign(h, h + 3 * L1);
+      measures_from_histograms_rect(r.hist.data(), r.hist.data() + L1, r.hist.data() + 2 * L1,
+                                    p.z.hl, p.z.n, p.z.n2, in[q].st.l_min, in[q].st.v_min,
+                                    in[q].st.w_min, &r.meas);
     } else if (first_err == RQA_OK) {
       first_err = r.status;
       err_ = r.status == RQA_ENAN       ? "series contains NaN or infinite values"
@@ -555,7 +627,10 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     }
     rqa_stats_t& s = r.stats;
     s.n_vec = p.z.n;
-    s.pairs = pair_count(p.z.n, in[q].st.theiler);
+    s.n_cols = p.z.n2;
+    s.cross = p.z.cross ? 1 : 0;
+    s.pairs = p.z.cross ? cross_cell_count(p.z.n, p.z.n2, std::min<int64_t>(in[q].st.theiler, p.z.hl))
+                        : pair_count(p.z.n, in[q].st.theiler);
     s.rechecks = static_cast<int64_t>(cnt[CNT_RECHECKS]);
     s.precision_used = p.z.f64 ? RQA_PREC_FP64 : RQA_PREC_FP32_RECHECK;
     s.band = p.z.f64 ? 0.0 : d.band_rel;

@@ -19,12 +19,19 @@ struct SeriesInput {
   const double* host = nullptr;  // copied to the device
   const double* dev = nullptr;   // used in place (caller's device memory)
   int64_t N = 0;
+  // cross recurrence (Sect. 3.3): the column series, host or device
+  bool cross = false;
+  const double* host2 = nullptr;
+  const double* dev2 = nullptr;
+  int64_t N2 = 0;
 };
 
 struct SeriesResult {
   int status = RQA_OK;
-  int64_t n = 0;
-  std::vector<uint64_t> hist;  // 3 * (n + 1): diagonal, vertical, white vertical
+  int64_t n = 0;               // rows (embedded vectors of the series)
+  int64_t n2 = 0;              // columns (== n for RQA)
+  int64_t hl = 0;              // histogram length - 1: n, or max(n, n2)
+  std::vector<uint64_t> hist;  // 3 * (hl + 1): diagonal, vertical, white vertical
   rqa_measures_t meas{};
   rqa_stats_t stats{};
 };
@@ -43,6 +50,11 @@ size_t series_device_bytes(const rqa_settings& st, int64_t N);
 void measures_from_histograms(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
                               int64_t n, int32_t l_min, int32_t v_min, int32_t w_min,
                               rqa_measures_t* out);
+// The same for a rows x cols (cross-recurrence) matrix with histograms of
+// length hl + 1; RR = RP / (rows * cols).
+void measures_from_histograms_rect(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
+                                   int64_t hl, int64_t rows, int64_t cols, int32_t l_min,
+                                   int32_t v_min, int32_t w_min, rqa_measures_t* out);
 
 class Engine {
  public:

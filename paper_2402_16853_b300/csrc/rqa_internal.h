@@ -18,6 +18,12 @@ struct SeriesDesc {
   int32_t sw;           // columns per CTA strip
   double eps;
   double band_override; // < 0: automatic
+  // ---- cross recurrence (Sect. 3.3): the columns come from a second series
+  const double* s2;     // FP64 column series (device); == s for RQA
+  float* xe2;           // its embedded FP32 vectors; == xe for RQA
+  int64_t N2, n2;       // its length and vector count; == N, n for RQA
+  int64_t hl;           // longest possible line: n (RQA) or max(n, n2)
+  int32_t cross;        // 1: rows from s, columns from s2, no symmetry
   // ---- filled by the prepare kernel
   double center, scale; // x32 = fl32((s - center) * scale)
   float thr;            // FP32 threshold: eps*scale (L1, max) or its square (L2)
@@ -25,7 +31,7 @@ struct SeriesDesc {
   double band_rel;      // band / eps (eps^2 for L2)
   double bound_rel;     // proven sufficient band, same units
   // ---- outputs (device)
-  unsigned long long* hist;   // [3][n+1]: upper diagonals, vertical, white vertical
+  unsigned long long* hist;   // [3][hl+1]: upper diagonals, vertical, white vertical
   uint16_t* row_a;            // boundary descriptors, strip-triangular layout
   uint16_t* row_z;
   uint16_t* dia_a;
@@ -34,6 +40,17 @@ struct SeriesDesc {
   uint32_t* rowend;           // [n] run of row i touching column i+1
   unsigned long long* counters;  // [0] rechecks, [1] status (rqa_status)
 };
+
+// Fill the column-series fields of an RQA (symmetric) descriptor: the
+// columns are the rows' own vectors.
+__host__ __device__ inline void desc_set_symmetric(SeriesDesc& d) {
+  d.s2 = d.s;
+  d.xe2 = d.xe;
+  d.N2 = d.N;
+  d.n2 = d.n;
+  d.hl = d.n;
+  d.cross = 0;
+}
 
 enum { HIST_DIAG = 0, HIST_VERT = 1, HIST_WHITE = 2 };
 enum { CNT_RECHECKS = 0, CNT_STATUS = 1, CNT_WORDS = 2 };
@@ -45,6 +62,16 @@ __host__ __device__ inline int64_t strip_offset(int64_t n, int64_t sw, int64_t Q
 }
 __host__ __device__ inline int64_t num_strips(int64_t n, int64_t sw) {
   return n >= 2 ? (n - 2) / sw + 1 : 0;
+}
+
+// Cross recurrence: every strip spans all n1 rows, so strip Q holds the
+// n1 + sw - 1 diagonals k = J1(Q) - sw - (n1 - 1) .. J1(Q) - 1 that can
+// cross it, with J1(Q) = n2 - Q*sw.
+__host__ __device__ inline int64_t cross_strip_diags(int64_t n1, int64_t sw) {
+  return n1 + sw - 1;
+}
+__host__ __device__ inline int64_t cross_num_strips(int64_t n2, int64_t sw) {
+  return n2 >= 1 ? (n2 - 1) / sw + 1 : 0;
 }
 
 struct Item {

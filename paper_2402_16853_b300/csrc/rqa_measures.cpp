@@ -49,17 +49,27 @@ double entropy(const uint64_t* h, int64_t n, int64_t lo, uint64_t count) {
 
 }  // namespace
 
+void measures_from_histograms_rect(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
+                                   int64_t n, int64_t rows, int64_t cols, int32_t l_min,
+                                   int32_t v_min, int32_t w_min, rqa_measures_t* out);
+
 void measures_from_histograms(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
                               int64_t n, int32_t l_min, int32_t v_min, int32_t w_min,
                               rqa_measures_t* out) {
+  measures_from_histograms_rect(hd, hv, hw, n, n, n, l_min, v_min, w_min, out);
+}
+
+void measures_from_histograms_rect(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
+                                   int64_t n, int64_t rows, int64_t cols, int32_t l_min,
+                                   int32_t v_min, int32_t w_min, rqa_measures_t* out) {
   const Sums d = sums_from(hd, n, l_min), d_all = sums_from(hd, n, 1);
   const Sums v = sums_from(hv, n, v_min), v_all = sums_from(hv, n, 1);
   const Sums w = sums_from(hw, n, w_min);
   // every recurrence point lies on exactly one vertical line
   const uint64_t rp = v_all.cells;
-  out->n_vec = n;
+  out->n_vec = rows;
   out->recurrence_points = static_cast<int64_t>(rp);
-  const double nn = static_cast<double>(n) * static_cast<double>(n);
+  const double nn = static_cast<double>(rows) * static_cast<double>(cols);
   out->rr = static_cast<double>(rp) / nn;
   out->det = static_cast<double>(d.cells) / static_cast<double>(d_all.cells);
   out->l = static_cast<double>(d.cells) / static_cast<double>(d.count);

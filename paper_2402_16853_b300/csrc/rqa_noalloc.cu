@@ -182,6 +182,7 @@ extern "C" int rqa_run_noalloc(const rqa_settings* settings, const double* dev_s
   init.colend = reinterpret_cast<uint32_t*>(base + o_ends);
   init.rowend = init.colend + n;
   init.counters = reinterpret_cast<unsigned long long*>(base + o_cnt);
+  desc_set_symmetric(init);
   SeriesDesc* d_sd = reinterpret_cast<SeriesDesc*>(base + o_sd);
   Item* d_items = reinterpret_cast<Item*>(base + o_items);
   int* d_queue = reinterpret_cast<int*>(base + o_queue);
@@ -195,7 +196,7 @@ extern "C" int rqa_run_noalloc(const rqa_settings* settings, const double* dev_s
   launch_prepare(d_sd, 1, st);
   if (!f64) launch_embed(d_sd, 1, n * mp, sms, st);
   if (nstrips > 0) {
-    TileFn fn = tile_kernel_for(s.m, s.norm, tc.cols, f64);
+    TileFn fn = tile_kernel_for(s.m, s.norm, tc.cols, f64, false);
     if (!fn) return fail(RQA_EINVAL, "no tile kernel for this (m, norm)");
     const size_t smem = tile_smem_for(s.m, s.norm, f64, tc.warps, tc.cols);
     if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
@@ -218,7 +219,7 @@ extern "C" int rqa_run_noalloc(const rqa_settings* settings, const double* dev_s
                               dim3(32 * tc.warps), args, smem, st)) != cudaSuccess)
       return fail(RQA_ECUDA, std::string("tile kernel launch: ") + cudaGetErrorString(e));
   }
-  launch_merges(d_sd, 1, n, sms, st);
+  launch_merges(d_sd, 1, n, true, false, sms, st);
   if ((e = cudaGetLastError()) != cudaSuccess)
     return fail(RQA_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   unsigned long long status = 0;

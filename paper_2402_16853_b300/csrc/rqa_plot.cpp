@@ -1,4 +1,5 @@
-// rqa_plot.cpp -- rqa_recurrence_plot(): a window of the recurrence matrix,
+// rqa_plot.cpp -- rqa_recurrence_plot() and rqa_cross_recurrence_plot(): a
+// window of the recurrence (or cross-recurrence) matrix,
 // bit-packed, computed on the GPU with the same decisions as rqa_run (the
 // paper's RecurrencePlotComputation, Table 2; Sect. 2 describes the plot as
 // the visual form of the matrix).  The output is a plain buffer; turning it
@@ -23,19 +24,28 @@ int plot_fail(int code, const std::string& m) {
 
 extern "C" const char* rqa_plot_last_error(void) { return t_plot_error.c_str(); }
 
-extern "C" int rqa_recurrence_plot(const rqa_settings* settings, const double* host_series,
-                                   int64_t n_points, int64_t i0, int64_t j0, int64_t rows,
-                                   int64_t cols, uint32_t* out_bits) {
+namespace {
+
+// One plot window.  host_y == nullptr: the RQA matrix of host_x; otherwise
+// the cross-recurrence matrix, rows from host_x and columns from host_y.
+int plot_common(const rqa_settings* settings, const double* host_x, int64_t nx,
+                const double* host_y, int64_t ny, int64_t i0, int64_t j0, int64_t rows,
+                int64_t cols, uint32_t* out_bits) {
   using namespace rqa;
   t_plot_error.clear();
   std::string msg;
   int rc = validate_settings(settings, &msg);
   if (rc != RQA_OK) return plot_fail(rc, msg);
-  if (!host_series || !out_bits) return plot_fail(RQA_EINVAL, "NULL pointer");
+  const bool cross = host_y != nullptr;
+  if (!host_x || !out_bits) return plot_fail(RQA_EINVAL, "NULL pointer");
   if (rows < 0 || cols < 0 || i0 < 0 || j0 < 0) return plot_fail(RQA_EINVAL, "negative window");
-  const int64_t n = n_points - static_cast<int64_t>(settings->m - 1) * settings->tau;
-  if (n_points < 1 || n < 1) return plot_fail(RQA_ESHORT, "series shorter than the embedding");
-  if (n > RQA_MAX_N) return plot_fail(RQA_ETOOBIG, "more than RQA_MAX_N embedded vectors");
+  const int64_t span = static_cast<int64_t>(settings->m - 1) * settings->tau;
+  const int64_t n = nx - span;
+  const int64_t n2 = cross ? ny - span : n;
+  if (nx < 1 || n < 1 || (cross && (ny < 1 || n2 < 1)))
+    return plot_fail(RQA_ESHORT, "series shorter than the embedding");
+  if (n > RQA_MAX_N || n2 > RQA_MAX_N)
+    return plot_fail(RQA_ETOOBIG, "more than RQA_MAX_N embedded vectors");
   const int64_t wpr = (cols + 31) / 32;
   const size_t out_bytes = sizeof(uint32_t) * static_cast<size_t>(rows) * wpr;
   if (out_bytes > (size_t(4) << 30)) return plot_fail(RQA_ETOOBIG, "plot above 4 GiB");
@@ -50,8 +60,10 @@ extern "C" int rqa_recurrence_plot(const rqa_settings* settings, const double* h
   const size_t o_sd = 0;
   const size_t o_cnt = align256(sizeof(SeriesDesc));
   const size_t o_s = o_cnt + 256;
-  const size_t o_xe = o_s + align256(sizeof(double) * static_cast<size_t>(n_points));
-  const size_t o_out = o_xe + align256(sizeof(float) * static_cast<size_t>(n) * mp);
+  const size_t o_s2 = o_s + align256(sizeof(double) * static_cast<size_t>(nx));
+  const size_t o_xe = o_s2 + (cross ? align256(sizeof(double) * static_cast<size_t>(ny)) : 0);
+  const size_t o_xe2 = o_xe + align256(sizeof(float) * static_cast<size_t>(n) * mp);
+  const size_t o_out = o_xe2 + (cross ? align256(sizeof(float) * static_cast<size_t>(n2) * mp) : 0);
   const size_t total = o_out + align256(out_bytes);
   unsigned char* base = nullptr;
   if ((e = cudaMalloc(&base, total)) != cudaSuccess) {
@@ -62,7 +74,7 @@ extern "C" int rqa_recurrence_plot(const rqa_settings* settings, const double* h
   std::memset(&d, 0, sizeof(d));
   d.s = reinterpret_cast<const double*>(base + o_s);
   d.xe = f64 ? nullptr : reinterpret_cast<float*>(base + o_xe);
-  d.N = n_points;
+  d.N = nx;
   d.n = n;
   d.m = settings->m;
   d.tau = settings->tau;
@@ -72,6 +84,15 @@ extern "C" int rqa_recurrence_plot(const rqa_settings* settings, const double* h
   d.eps = settings->eps;
   d.band_override = settings->band_override;
   d.counters = reinterpret_cast<unsigned long long*>(base + o_cnt);
+  desc_set_symmetric(d);
+  if (cross) {
+    d.s2 = reinterpret_cast<const double*>(base + o_s2);
+    d.xe2 = f64 ? nullptr : reinterpret_cast<float*>(base + o_xe2);
+    d.N2 = ny;
+    d.n2 = n2;
+    d.hl = n > n2 ? n : n2;
+    d.cross = 1;
+  }
   SeriesDesc* d_sd = reinterpret_cast<SeriesDesc*>(base + o_sd);
   uint32_t* d_out = reinterpret_cast<uint32_t*>(base + o_out);
   cudaStream_t st = nullptr;
@@ -79,12 +100,14 @@ extern "C" int rqa_recurrence_plot(const rqa_settings* settings, const double* h
   rc = RQA_OK;
   if ((e = cudaMemsetAsync(base + o_cnt, 0, 256, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_sd, &d, sizeof(d), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(base + o_s, host_series, sizeof(double) * n_points,
-                           cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+      (e = cudaMemcpyAsync(base + o_s, host_x, sizeof(double) * nx, cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess ||
+      (cross && (e = cudaMemcpyAsync(base + o_s2, host_y, sizeof(double) * ny,
+                                     cudaMemcpyHostToDevice, st)) != cudaSuccess)) {
     rc = plot_fail(RQA_ECUDA, cudaGetErrorString(e));
   } else {
     launch_prepare(d_sd, 1, st);
-    if (!f64) launch_embed(d_sd, 1, n * mp, sms, st);
+    if (!f64) launch_embed(d_sd, 1, (n + (cross ? n2 : 0)) * mp, sms, st);
     launch_plot(d_sd, i0, j0, rows, cols, d_out, f64 ? 1 : 0, sms, st);
     if ((e = cudaGetLastError()) != cudaSuccess ||
         (e = cudaMemcpyAsync(out_bits, d_out, out_bytes, cudaMemcpyDeviceToHost, st)) !=
@@ -98,4 +121,20 @@ extern "C" int rqa_recurrence_plot(const rqa_settings* settings, const double* h
   }
   cudaFree(base);
   return rc;
+}
+
+}  // namespace
+
+extern "C" int rqa_recurrence_plot(const rqa_settings* settings, const double* host_series,
+                                   int64_t n_points, int64_t i0, int64_t j0, int64_t rows,
+                                   int64_t cols, uint32_t* out_bits) {
+  return plot_common(settings, host_series, n_points, nullptr, 0, i0, j0, rows, cols, out_bits);
+}
+
+extern "C" int rqa_cross_recurrence_plot(const rqa_settings* settings, const double* host_x,
+                                         int64_t nx, const double* host_y, int64_t ny,
+                                         int64_t i0, int64_t j0, int64_t rows, int64_t cols,
+                                         uint32_t* out_bits) {
+  if (!host_y) return plot_fail(RQA_EINVAL, "NULL pointer");
+  return plot_common(settings, host_x, nx, host_y, ny, i0, j0, rows, cols, out_bits);
 }

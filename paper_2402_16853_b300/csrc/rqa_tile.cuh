@@ -363,6 +363,28 @@ __device__ __forceinline__ bool exact_decision(const double* __restrict__ s, int
   return acc <= eps;
 }
 
+// The same decision for a row vector of series a and a column vector of
+// series b (cross recurrence).
+template <int NORM>
+__device__ __forceinline__ bool exact_decision2(const double* __restrict__ a,
+                                                const double* __restrict__ b, int64_t i,
+                                                int64_t j, int m, int tau, double eps) {
+  double acc = 0.0;
+  for (int k = 0; k < m; ++k) {
+    const double diff = __dsub_rn(a[i + (int64_t)k * tau], b[j + (int64_t)k * tau]);
+    if (NORM == 0) {
+      const double ad = fabs(diff);
+      if (ad > acc) acc = ad;
+    } else if (NORM == 2) {
+      acc = __dadd_rn(acc, fabs(diff));
+    } else {
+      acc = __dadd_rn(acc, __dmul_rn(diff, diff));
+    }
+  }
+  if (NORM == 1) acc = __dsqrt_rn(acc);
+  return acc <= eps;
+}
+
 // Same decision with both vectors already in registers (FP64 path).
 template <int M, int NORM>
 __device__ __forceinline__ bool exact_decision_regs(const double* xr, const double* xc,
@@ -400,6 +422,18 @@ __device__ __forceinline__ bool spin_until_ge(volatile int* ctr, int target,
   return true;
 }
 
+// Cells of column j, rows r0 .. r0+31, that can recur: RQA keeps the rows
+// above the line of identity outside the Theiler window (i <= j - w); cross
+// recurrence keeps the rows below n outside |i - j| < w.
+template <bool XR>
+__device__ __forceinline__ uint32_t live_mask(int j, int r0, int n, int w) {
+  if (j < 0) return 0u;
+  if constexpr (XR)
+    return lowmask(n - r0) & ~(lowmask(j + w - r0) & ~lowmask(j - w + 1 - r0));
+  else
+    return lowmask(j - r0) & lowmask(j - w - r0 + 1);
+}
+
 // Row buffer layout: FP32 rows hold each coordinate twice (x0 x0 x1 x1 ...)
 // for the packed L2 path, once otherwise; FP64 rows hold m doubles.
 template <int M, int NORM, bool F64>
@@ -417,7 +451,7 @@ inline size_t tile_smem_bytes(int warps, int row_elems, int elem_bytes, int cols
 }
 
 // ------------------------------------------------------------------ kernel
-template <int M, int NORM, int C, bool F64>
+template <int M, int NORM, int C, bool F64, bool XR>
 __global__ void __launch_bounds__(256, 3)
 tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, int nitems,
             int* __restrict__ queue) {
@@ -466,12 +500,15 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
     unsigned long long rechecks = 0;
     const Item wi = items[it];
     const SeriesDesc* Sp = sd + wi.series;
-    const int n = (int)Sp->n;
+    const int n = (int)Sp->n;                    // rows
+    const int ncol = XR ? (int)Sp->n2 : n;       // columns
     const int SW = Sp->sw;
     const int tau = Sp->tau;
     const int wtheiler = Sp->w;
     const double* __restrict__ sser = Sp->s;
     const float* __restrict__ xe = Sp->xe;
+    const double* __restrict__ sser2 = XR ? Sp->s2 : Sp->s;   // column series
+    const float* __restrict__ xe2 = XR ? Sp->xe2 : Sp->xe;
     const int mp = Sp->mp;
     const double eps = Sp->eps;
     uint32_t* __restrict__ colend = Sp->colend;
@@ -479,19 +516,25 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
     uint16_t* __restrict__ row_z = Sp->row_z;
     uint16_t* __restrict__ dia_a = Sp->dia_a;
     uint16_t* __restrict__ dia_z = Sp->dia_z;
-    const int J1 = n - wi.strip * SW;                 // strip: [J1-SW, J1)
-    const int64_t off = strip_offset(n, SW, wi.strip);
+    const int J1 = ncol - wi.strip * SW;              // strip: [J1-SW, J1)
+    // descriptors of diagonal k sit at off + k - klo (RQA: k >= 1 in a
+    // strip-triangular layout; cross: the n + SW - 1 diagonals of the strip)
+    const int64_t off = XR ? (int64_t)wi.strip * cross_strip_diags(n, SW)
+                           : strip_offset(n, SW, wi.strip);
+    const int klo = XR ? J1 - SW - (n - 1) : 1;
     const int jw1 = J1 - warp * 32 * C;              // warp: [jw0, jw1)
     const int jw0 = jw1 - 32 * C;
-    const int wl_geo = (J1 - 2) / (32 * C);
+    const int wl_geo = XR ? (J1 - 1) / (32 * C) : (J1 - 2) / (32 * C);
     const int wlast = wl_geo < NW - 1 ? wl_geo : NW - 1;
-    const HistSink hs{sh_hist, Sp->hist, (uint32_t)n, &Sp->counters[CNT_STATUS]};
+    const int nh = XR ? (int)Sp->hl : n;             // longest possible line
+    const HistSink hs{sh_hist, Sp->hist, (uint32_t)nh, &Sp->counters[CNT_STATUS]};
 
     if (warp <= wlast) {
       const bool leftmost = warp == wlast;
       const int jmax = jw1 - 1;
-      const int bhi = (jmax - 1) >> 5;
-      const int bhi_left = leftmost ? -1 : ((jmax - 32 * C - 1) >> 5);
+      // RQA: rows above the line of identity; cross: all n rows
+      const int bhi = XR ? (n - 1) >> 5 : (jmax - 1) >> 5;
+      const int bhi_left = leftmost ? -1 : XR ? bhi : ((jmax - 32 * C - 1) >> 5);
       uint32_t* ring_in = warp > 0 ? ring + (warp - 1) * RING * 64 : nullptr;
       uint32_t* ring_out = !leftmost ? ring + warp * RING * 64 : nullptr;
       int seq_in = 0, seq_out = 0;
@@ -508,15 +551,15 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
 #pragma unroll
         for (int k = 0; k < M; ++k) {
           if constexpr (F64) {
-            xc[c][k] = j >= 0 ? sser[j + k * tau] : 0.0;
+            xc[c][k] = j >= 0 ? sser2[j + k * tau] : 0.0;
           } else if constexpr (PACKED) {
             if (c % 2 == 1) {
               const int j0 = j - 32;
-              xc2[c / 2][k] = f2_pack(j0 >= 0 ? xe[(int64_t)j0 * mp + k] : 0.f,
-                                      j >= 0 ? xe[(int64_t)j * mp + k] : 0.f);
+              xc2[c / 2][k] = f2_pack(j0 >= 0 ? xe2[(int64_t)j0 * mp + k] : 0.f,
+                                      j >= 0 ? xe2[(int64_t)j * mp + k] : 0.f);
             }
           } else {
-            xc[c][k] = j >= 0 ? xe[(int64_t)j * mp + k] : 0.f;
+            xc[c][k] = j >= 0 ? xe2[(int64_t)j * mp + k] : 0.f;
           }
         }
         cst_s[c * 32 + lane] = ST_FLAG;
@@ -605,8 +648,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
 #pragma unroll
           for (int c = 0; c < C; ++c) {
             const int j = jw0 + 32 * c + lane;
-            const uint32_t live =
-                j < 0 ? 0u : lowmask(j - r0) & lowmask(j - wtheiler - r0 + 1);
+            const uint32_t live = live_mask<XR>(j, r0, n, wtheiler);
             // packed: sign bit = recurrent; scalar: sign bit = not recurrent
             uint32_t R = (PACKED ? Nw[c] : ~Nw[c]) & live;
             if (mn[c] <= band && live) {
@@ -630,7 +672,11 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
                 }
                 const float acc = pair_margin<M, NORM>(xr, xcc, thr);
                 if (fabsf(acc) <= band) {
-                  const bool r = exact_decision<NORM>(sser, r0 + t, j, M, tau, eps);
+                  bool r;
+                  if constexpr (XR)
+                    r = exact_decision2<NORM>(sser, sser2, r0 + t, j, M, tau, eps);
+                  else
+                    r = exact_decision<NORM>(sser, r0 + t, j, M, tau, eps);
                   R = r ? (R | (1u << t)) : (R & ~(1u << t));
                   ++rechecks;
                 }
@@ -655,8 +701,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
 #pragma unroll
           for (int c = 0; c < C; ++c) {
             const int j = jw0 + 32 * c + lane;
-            const uint32_t live =
-                j < 0 ? 0u : lowmask(j - r0) & lowmask(j - wtheiler - r0 + 1);
+            const uint32_t live = live_mask<XR>(j, r0, n, wtheiler);
             Rw_s[c * 32 + lane] = Rf[c] & live;
           }
         }
@@ -674,7 +719,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           if (!ok) break;
           __threadfence_block();
           const volatile uint32_t* slot = ring_in + (seq_in % RING) * 64;
-          rst = slot[lane];
+          if constexpr (!XR) rst = slot[lane];
           dL = slot[32 + lane];
           __syncwarp();
           if (lane == 0) cons[warp] = seq_in + 1;
@@ -693,11 +738,18 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           const int j = col0 + lane;
           const uint32_t R = Rw_s[c * 32 + lane];
 
-          // ---- operator III, upper part of full column j (rows < j)
+          // ---- operator III, upper part of full column j (rows < j); cross:
+          // the whole column, whose first run ends at the bottom border
           {
-            const int vt = j < 0 ? 0 : clamp32(j - r0);
+            const int vt = j < 0 ? 0 : clamp32((XR ? n : j) - r0);
             auto emitc = [&](uint32_t col, uint32_t len) { hs.add2(col, len); };
-            auto firstc = [&](uint32_t col, uint32_t len) { colend[j] = len | (col << 31); };
+            auto firstc = [&](uint32_t col, uint32_t len) {
+              if constexpr (XR) {
+                if (len) hs.add2(col, len);
+              } else {
+                colend[j] = len | (col << 31);
+              }
+            };
             if (vt == 32)
               cst_s[c * 32 + lane] = scan2_full(R, cst_s[c * 32 + lane], sc, emitc, firstc);
             else if (vt > 0)
@@ -705,7 +757,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           }
 
           // ---- operator III, lower part of full column irow = upper row irow
-          {
+          if constexpr (!XR) {
             const uint32_t RW = transpose32(R, lane);
             const int lo = irow + 1 - col0;  // first valid bit of the row
             if (lo <= 31 && !(rst & ST_DONE) && row_valid) {
@@ -734,7 +786,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             const int k = col0 - r0 + d;  // diagonal of this sub-block's upper segment
             auto emitd = [&](uint32_t len) { hs.add(HIST_DIAG, len); };
             auto firstd = [&](uint32_t len) {
-              if (k >= 1) dia_a[off + k - 1] = (uint16_t)len;
+              if (k >= klo) dia_a[off + k - klo] = (uint16_t)len;
             };
             if (c == C - 1) {
               // upper segment only (bits 31..d), entering from the right
@@ -758,7 +810,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             dL = scan_black(
                 Dprev & segL, segL, d - 1, 0, du, [&](uint32_t len) { hs.add(HIST_DIAG, len); },
                 [&](uint32_t len) {
-                  if (k >= 1) dia_a[off + k - 1] = (uint16_t)len;
+                  if (k >= klo) dia_a[off + k - klo] = (uint16_t)len;
                 });
         }
         bufo ^= 1;
@@ -769,7 +821,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
 
         // ---- carries leaving to the left
         if (leftmost) {
-          if (!(rst & ST_DONE) && row_valid) {
+          if (!XR && !(rst & ST_DONE) && row_valid) {
             const uint32_t len = rst & ST_LEN, col = (rst >> 28) & 1u;
             const uint32_t same = (rst >> 29) & 1u;
             if (len > 0) {
@@ -778,14 +830,14 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             }
           }
           const int kx = jw0 - r0 + lane - 32;  // diagonal leaving through the left edge
-          if (kx >= 1)
-            dia_z[off + kx - 1] = (uint16_t)((dL & ST_LEN) | ((dL & DG_EDGE) ? 0x8000u : 0u));
+          if (kx >= klo)
+            dia_z[off + kx - klo] = (uint16_t)((dL & ST_LEN) | ((dL & DG_EDGE) ? 0x8000u : 0u));
         } else if (b <= bhi_left) {
           if (lane == 0) ok = spin_until_ge(cons + (warp + 1), seq_out - RING + 1, &s_abort);
           ok = __shfl_sync(FULL, ok, 0);
           if (!ok) break;
           uint32_t* slot = ring_out + (seq_out % RING) * 64;
-          slot[lane] = rst;
+          if constexpr (!XR) slot[lane] = rst;
           slot[32 + lane] = dL;
           __syncwarp();
           __threadfence_block();
@@ -799,17 +851,17 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
 #pragma unroll 1
         for (int c = 0; c < C; ++c) {
           const int j = jw0 + 32 * c + lane;
-          if (j >= 1) {
+          if (j >= (XR ? 0 : 1)) {
             const uint32_t st = cst_s[c * 32 + lane];
             const uint32_t len = st & ST_LEN, col = (st >> 28) & 1u;
             if (len > 0) {
-              if (st & ST_FLAG)
+              if (!XR && (st & ST_FLAG))
                 colend[j] = len | (col << 31);
               else
                 hs.add2(col, len);
             }
             const uint32_t du = dU_s[bufo * C * 32 + c * 32 + lane];  // k = j ends at (0, j)
-            dia_z[off + j - 1] = (uint16_t)((du & ST_LEN) | ((du & DG_EDGE) ? 0x8000u : 0u));
+            dia_z[off + j - klo] = (uint16_t)((du & ST_LEN) | ((du & DG_EDGE) ? 0x8000u : 0u));
           }
         }
       }
@@ -819,7 +871,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
     if (s_abort && threadIdx.x == 0)
       atomicExch(&Sp->counters[CNT_STATUS], 6ull /* RQA_ETIMEOUT */);
     // flush the strip's histograms
-    const int64_t stride = (int64_t)n + 1;
+    const int64_t stride = (int64_t)(XR ? (int)Sp->hl : n) + 1;
     for (int q = threadIdx.x; q < 3 * HB; q += blockDim.x) {
       const uint32_t v = sh_hist[q];
       if (v) atomicAdd(&Sp->hist[(q / HB) * stride + (q % HB)], (unsigned long long)v);

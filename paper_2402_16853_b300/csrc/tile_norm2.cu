@@ -8,7 +8,8 @@ namespace rqa {
 template <int M>
 static TileFn pick(int cols, bool f64) {
   if (cols != 4) return nullptr;
-  return f64 ? (TileFn)tile_kernel<M, 2, 4, true> : (TileFn)tile_kernel<M, 2, 4, false>;
+  return f64 ? (TileFn)tile_kernel<M, 2, 4, true, false>
+             : (TileFn)tile_kernel<M, 2, 4, false, false>;
 }
 
 TileFn tile_kernel_norm2(int m, int cols, bool f64) {

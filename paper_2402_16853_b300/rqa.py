@@ -79,7 +79,7 @@ class _CStats(ctypes.Structure):
                 ("ctas", ctypes.c_int32), ("kernel_ms", ctypes.c_float),
                 ("total_ms", ctypes.c_float), ("h2d_bytes", ctypes.c_int64),
                 ("d2h_bytes", ctypes.c_int64), ("launches", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("cross", ctypes.c_int32), ("n_cols", ctypes.c_int64)]
 
 
 MEASURE_FIELDS = list(_MEAS_D + _MEAS_I)
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH):
         "rqa_create": (c.c_int, [P(_CSettings), P(vp)]),
         "rqa_run": (c.c_int, [vp, P(c.c_double), c.c_int64]),
         "rqa_run_device": (c.c_int, [vp, vp, c.c_int64, vp]),
+        "rqa_run_cross": (c.c_int, [vp, P(c.c_double), c.c_int64, P(c.c_double), c.c_int64]),
+        "rqa_run_cross_device": (c.c_int, [vp, vp, c.c_int64, vp, c.c_int64, vp]),
         "rqa_measures": (c.c_int, [vp, P(_CMeasures)]),
         "rqa_histogram": (c.c_int, [vp, c.c_int32, P(c.c_uint64), c.c_int64, P(c.c_int64)]),
         "rqa_stats": (c.c_int, [vp, P(_CStats)]),
@@ -125,6 +127,10 @@ def load(path: str = LIB_PATH):
         "rqa_server_destroy": (None, [vp]),
         "rqa_recurrence_plot": (c.c_int, [P(_CSettings), P(c.c_double), c.c_int64, c.c_int64,
                                           c.c_int64, c.c_int64, c.c_int64, P(c.c_uint32)]),
+        "rqa_cross_recurrence_plot": (c.c_int, [P(_CSettings), P(c.c_double), c.c_int64,
+                                                P(c.c_double), c.c_int64, c.c_int64,
+                                                c.c_int64, c.c_int64, c.c_int64,
+                                                P(c.c_uint32)]),
         "rqa_plot_last_error": (c.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -211,6 +217,34 @@ class RQA:
             n_in = len(s)
         self._check(rc, "rqa_run")
         self.n = n_in - (self.settings.m - 1) * self.settings.tau
+        return self.measures()
+
+    def run_cross(self, x, y, stream=None) -> dict:
+        """Cross recurrence of two series (rows: vectors of x, columns:
+        vectors of y), both host arrays or both CUDA float64 tensors.
+        Returns the measures; histograms / stats / sample then describe the
+        n1 x n2 cross matrix."""
+        lib = load()
+        if hasattr(x, "is_cuda") and x.is_cuda:
+            import torch
+            tx, ty = x.contiguous(), y.contiguous()
+            if tx.dtype != torch.float64 or ty.dtype != torch.float64 or not ty.is_cuda:
+                raise TypeError("device series must both be CUDA float64 tensors")
+            if stream is None:
+                stream = torch.cuda.current_stream(tx.device)
+            sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+            rc = lib.rqa_run_cross_device(self._h, ctypes.c_void_p(tx.data_ptr()), tx.numel(),
+                                          ctypes.c_void_p(ty.data_ptr()), ty.numel(),
+                                          ctypes.c_void_p(sp))
+            self._keep = (tx, ty)
+        else:
+            a, b = _f64(x), _f64(y)
+            P = ctypes.POINTER(ctypes.c_double)
+            rc = lib.rqa_run_cross(self._h, a.ctypes.data_as(P), len(a), b.ctypes.data_as(P),
+                                   len(b))
+            self._keep = (a, b)
+        self._check(rc, "rqa_run_cross")
+        self.n = self.stats()["n_vec"]
         return self.measures()
 
     def measures(self) -> dict:
@@ -373,6 +407,30 @@ def recurrence_plot(settings: Settings, series, i0: int = 0, j0: int = 0,
                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
     if rc:
         raise RQAError(rc, "rqa_recurrence_plot", load().rqa_plot_last_error().decode())
+    if packed:
+        return out
+    bits = np.unpackbits(out.view(np.uint8), axis=1, bitorder="little")
+    return bits[:, :cols]
+
+
+def cross_recurrence_plot(settings: Settings, x, y, i0: int = 0, j0: int = 0,
+                          rows: Optional[int] = None, cols: Optional[int] = None,
+                          packed: bool = False):
+    """A window of the cross-recurrence matrix of x (rows) and y (columns),
+    in the layout of recurrence_plot()."""
+    a, b = _f64(x), _f64(y)
+    span = (settings.m - 1) * settings.tau
+    rows = len(a) - span - i0 if rows is None else rows
+    cols = len(b) - span - j0 if cols is None else cols
+    wpr = (cols + 31) // 32
+    out = np.zeros((max(rows, 0), wpr), dtype=np.uint32)
+    cs = _cs(settings)
+    P = ctypes.POINTER(ctypes.c_double)
+    rc = load().rqa_cross_recurrence_plot(ctypes.byref(cs), a.ctypes.data_as(P), len(a),
+                                          b.ctypes.data_as(P), len(b), i0, j0, rows, cols,
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    if rc:
+        raise RQAError(rc, "rqa_cross_recurrence_plot", load().rqa_plot_last_error().decode())
     if packed:
         return out
     bits = np.unpackbits(out.view(np.uint8), axis=1, bitorder="little")
