@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cross", action="store_true")
+    ap.add_argument("--no-sine", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--N", type=int, default=0,
@@ -314,6 +316,14 @@ def run_mine(args):
                               "measures_identical": bool(same)}
         del r64
 
+    # ---- cross recurrence of two AR(1) series (context line)
+    if not args.no_cross:
+        extra["cross"] = bench_cross(gp, params, dev, barrier, flush, peak)
+
+    # ---- the paper's own timing workload (context line)
+    if not args.no_sine:
+        extra["paper_sine"] = bench_sine(gp, dev, barrier)
+
     # ---- batched workload vs sequential single-series calls
     if not args.no_batch:
         extra["batched"] = bench_batch(gp, args, dev, barrier)
@@ -353,6 +363,62 @@ def run_mine(args):
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def bench_cross(gp, params, dev, barrier, flush, peak, N=524_288, steps=2):
+    """Cross recurrence (Sect. 3.3) of two independent AR(1) series of N
+    points each with the primary line's parameters: n1 x n2 cells per step."""
+    import torch
+    x = torch.tensor(synth.ar1(N, 1003, 0.95), dtype=torch.float64, device=dev)
+    y = torch.tensor(synth.ar1(N, 1007, 0.95), dtype=torch.float64, device=dev)
+    r = gp.RQA(gp.Settings(**params))
+    flush.fill_(1)
+    r.run_cross(x, y)
+    barrier()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    kms = []
+    e0.record(stream)
+    for _ in range(steps):
+        flush.fill_(1)
+        r.run_cross(x, y)
+        kms.append(r.stats()["kernel_ms"])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t = e0.elapsed_time(e1) / 1e3 / steps
+    st = r.stats()
+    cells = float(st["n_vec"]) * st["n_cols"]
+    k_ms = float(np.mean(kms))
+    ops = st["pairs"] * (2 * params["m"] + 1)
+    achieved = ops / (k_ms / 1e3) / 1e12
+    return {"workload": f"AR(1) x AR(1), N = {N} each (seeds 1003, 1007), same parameters",
+            "value": cells / t, "unit": "cells/s", "ms_per_step": t * 1e3, "steps": steps,
+            "kernel_ms": k_ms, "roofline_frac": achieved / peak,
+            "kernel": f"tile_kernel<{params['m']},L2,4,fp32,cross>",
+            "rechecks": int(st["rechecks"]), "rr": r.measures()["rr"]}
+
+
+def bench_sine(gp, dev, barrier, steps=2):
+    """The paper's runtime experiment (Sect. 8.2): sin over 1,000,001 points,
+    m = 2, tau = 2, radius 1, no Theiler window, timed end to end from a host
+    series (copies, all kernels, histograms back, measures), as the paper
+    times total runtime.  The paper's figures are context on other hardware."""
+    s, p = synth.workload("sine_paper")
+    r = gp.RQA(gp.Settings(**p))
+    r.run(s)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        meas = r.run(s)
+    t = (time.perf_counter() - t0) / steps
+    n = meas["n_vec"]
+    return {"workload": "sin(linspace(0, 1000 pi, 1000001)), m=2, tau=2, eps=1, L2, w=0",
+            "seconds_per_run": t, "value": float(n) * n / t, "unit": "cells/s",
+            "l_max": meas["l_max"], "det": meas["det"],
+            "paper_seconds_context": {"4x GK104 (2x GTX 690)": 68.94, "1x GK104": 204.81,
+                                      "i7-3820 OpenCL": 1667.58,
+                                      "CRP 1.13z, 1 thread": 28480.09}}
 
 
 def bench_batch(gp, args, dev, barrier):
