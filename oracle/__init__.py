@@ -11,8 +11,9 @@ Table 3, defined after Marwan et al. 2007): the full n x n recurrence matrix
 of a time-delay embedded series under the L1 / L2 / L-infinity norm with a
 fixed radius and a Theiler window, the histograms of diagonal, vertical and
 white vertical line lengths over that full matrix, and the measures derived
-from them.  Readings of points the paper leaves open are listed at the top of
-``rqa_oracle.c``.
+from them; the same for the cross-recurrence matrix of two series (Sect. 3.3)
+and for a precomputed binary matrix (Sect. 9).  Readings of points the paper
+leaves open are listed at the top of ``rqa_oracle.c``.
 """
 from __future__ import annotations
 
@@ -122,6 +123,10 @@ def _load():
                                              P(ctypes.c_uint64), ctypes.c_int64,
                                              ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
                                              P(_CSettings), P(_CMeasures)]
+        lib.oracle_histograms_from_rect.restype = ctypes.c_uint64
+        lib.oracle_histograms_from_rect.argtypes = [
+            P(ctypes.c_uint8), ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+            P(ctypes.c_uint64), P(ctypes.c_uint64), P(ctypes.c_uint64)]
         lib.oracle_measures.restype = None
         lib.oracle_measures.argtypes = [P(ctypes.c_uint64), P(ctypes.c_uint64),
                                         P(ctypes.c_uint64), ctypes.c_int64,
@@ -245,4 +250,24 @@ def cross_rqa(series1, series2, st: Settings, threads: int = 0):
     _load().oracle_measures_rect(_uptr(hd), _uptr(hv), _uptr(hw), L, n1, n2, int(rp),
                                  ctypes.byref(cs), ctypes.byref(out))
     return {"hd": hd, "hv": hv, "hw": hw, "rp": int(rp), "n": n1, "cols": n2,
+            "measures": {f: getattr(out, f) for f in MEASURE_FIELDS}}
+
+
+def matrix_rqa(R, st: Settings):
+    """Lines and measures of a precomputed rows x cols 0/1 matrix R (cells
+    with |i - j| < st.theiler count as 0).  Same dict as cross_rqa()."""
+    R = np.ascontiguousarray(np.asarray(R) != 0, dtype=np.uint8)
+    if R.ndim != 2:
+        raise ValueError("R must be two-dimensional")
+    rows, cols = R.shape
+    L = max(rows, cols, 0)
+    hd, hv, hw = (np.zeros(L + 1, np.uint64) for _ in range(3))
+    rp = _load().oracle_histograms_from_rect(R.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                             rows, cols, int(st.theiler), _uptr(hd), _uptr(hv),
+                                             _uptr(hw))
+    out = _CMeasures()
+    cs = _cs(st)
+    _load().oracle_measures_rect(_uptr(hd), _uptr(hv), _uptr(hw), L, rows, cols, int(rp),
+                                 ctypes.byref(cs), ctypes.byref(out))
+    return {"hd": hd, "hv": hv, "hw": hw, "rp": int(rp), "n": rows, "cols": cols,
             "measures": {f: getattr(out, f) for f in MEASURE_FIELDS}}

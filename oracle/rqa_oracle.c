@@ -365,6 +365,65 @@ uint64_t oracle_cross_histograms(const double* s1, int64_t N1, const double* s2,
   return ones;
 }
 
+/* ------------------------------------------------------------------------
+ * A precomputed binary matrix (Sect. 9 lists the quantitative analysis of
+ * precomputed recurrence matrices as requested by users).  R holds rows x
+ * cols cells (row-major, 0 or 1) and is taken as given, except that cells
+ * with |i - j| < w count as 0, as for a computed matrix (reading R3).  Lines
+ * are runs along the rows + cols - 1 diagonals and down the cols columns,
+ * border-cut runs keeping their length (reading R4).  Histograms have
+ * max(rows, cols) + 1 entries.  Returns the number of 1-cells counted.
+ * ------------------------------------------------------------------------ */
+static int rect_cell(const uint8_t* R, int64_t cols, int64_t i, int64_t j, int32_t w) {
+  int64_t gap = i > j ? i - j : j - i;
+  if (gap < (int64_t)w) return 0;
+  return R[i * cols + j] != 0;
+}
+
+uint64_t oracle_histograms_from_rect(const uint8_t* R, int64_t rows, int64_t cols,
+                                     int32_t w, uint64_t* hd, uint64_t* hv,
+                                     uint64_t* hw) {
+  int64_t L = rows > cols ? rows : cols;
+  memset(hd, 0, sizeof(uint64_t) * (size_t)(L + 1));
+  memset(hv, 0, sizeof(uint64_t) * (size_t)(L + 1));
+  memset(hw, 0, sizeof(uint64_t) * (size_t)(L + 1));
+  if (rows <= 0 || cols <= 0) return 0;
+  for (int64_t k = -(rows - 1); k <= cols - 1; ++k) {
+    int64_t i = k >= 0 ? 0 : -k;
+    int prev = -1;
+    int64_t run = 0;
+    for (; i < rows && i + k < cols; ++i) {
+      int v = rect_cell(R, cols, i, i + k, w);
+      if (v == prev) {
+        run += 1;
+      } else {
+        if (prev >= 0) close_run(hd, NULL, prev, run);
+        prev = v;
+        run = 1;
+      }
+    }
+    if (prev >= 0) close_run(hd, NULL, prev, run);
+  }
+  uint64_t ones = 0;
+  for (int64_t j = 0; j < cols; ++j) {
+    int prev = -1;
+    int64_t run = 0;
+    for (int64_t i = 0; i < rows; ++i) {
+      int v = rect_cell(R, cols, i, j, w);
+      ones += (uint64_t)v;
+      if (v == prev) {
+        run += 1;
+      } else {
+        if (prev >= 0) close_run(hv, hw, prev, run);
+        prev = v;
+        run = 1;
+      }
+    }
+    if (prev >= 0) close_run(hv, hw, prev, run);
+  }
+  return ones;
+}
+
 /* Sum over l >= lo of h[l] and of l * h[l], exactly in 64-bit integers. */
 static void hist_sums(const uint64_t* h, int64_t n, int64_t lo, uint64_t* s0,
                       uint64_t* s1) {

@@ -51,6 +51,17 @@ CROSS_MUTANTS = {
                                      "    }\n#pragma omp critical"),
 }
 
+# Mistakes in the precomputed-matrix code, caught by the matrix pins.
+MATRIX_MUTANTS = {
+    "matrix_theiler_ignored": ("if (gap < (int64_t)w) return 0;", "if (gap < 0) return 0;"),
+    "matrix_drops_last_diagonal": ("for (int64_t k = -(rows - 1); k <= cols - 1; ++k)",
+                                   "for (int64_t k = -(rows - 1); k < cols - 1; ++k)"),
+    "matrix_diagonal_border_runs_dropped": (
+        "    if (prev >= 0) close_run(hd, NULL, prev, run);\n  }\n  uint64_t ones = 0;",
+        "  }\n  uint64_t ones = 0;"),
+    "matrix_any_nonzero_not_one": ("return R[i * cols + j] != 0;", "return R[i * cols + j] & 2;"),
+}
+
 
 def _run_pins(name, old, new, pins, tmp_path):
     src = open(SRC).read()
@@ -75,3 +86,9 @@ def test_pins_catch_mutant(name, tmp_path):
 def test_cross_pins_catch_mutant(name, tmp_path):
     old, new = CROSS_MUTANTS[name]
     _run_pins(name, old, new, "test_oracle_cross_pins.py", tmp_path)
+
+
+@pytest.mark.parametrize("name", sorted(MATRIX_MUTANTS))
+def test_matrix_pins_catch_mutant(name, tmp_path):
+    old, new = MATRIX_MUTANTS[name]
+    _run_pins(name, old, new, "test_oracle_matrix_pins.py", tmp_path)
