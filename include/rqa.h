@@ -136,7 +136,7 @@ typedef struct {
   int64_t h2d_bytes;      /* host-to-device bytes copied by the run           */
   int64_t d2h_bytes;      /* device-to-host bytes copied by the run           */
   int32_t launches;       /* kernels launched by the run                      */
-  int32_t cross;          /* 1 if the run was a cross recurrence              */
+  int32_t mode;           /* 0 RQA, 1 cross recurrence, 2 precomputed matrix  */
   int64_t n_cols;         /* columns: n_vec for RQA, n2 for cross recurrence  */
 } rqa_stats_t;
 
@@ -173,6 +173,23 @@ int rqa_run_cross(rqa_handle* h, const double* host_x, int64_t n_x,
 /* The same with both series in device memory, ordered on cuda_stream. */
 int rqa_run_cross_device(rqa_handle* h, const double* dev_x, int64_t n_x,
                          const double* dev_y, int64_t n_y, void* cuda_stream);
+/* Lines and measures of a precomputed binary matrix (Sect. 9 lists the
+ * analysis of precomputed recurrence matrices as a user request): `rows` x
+ * `cols` cells, row-major and bit-packed as rqa_recurrence_plot writes them
+ * (row r occupies ceil(cols/32) uint32 words, bit b of word w is column
+ * 32 w + b; bits past the last column are ignored).  The matrix is taken as
+ * given, except that cells with |i - j| < theiler count as 0; diagonal lines
+ * run along all rows + cols - 1 diagonals and vertical / white lines down the
+ * cols columns, as for cross recurrence, with RR = RP / (rows * cols) and
+ * histograms of max(rows, cols) + 1 entries.  The handle's m, tau, eps, norm
+ * and precision are not used.  rows, cols in 1..RQA_MAX_N; the library copies
+ * the host bits (rows * ceil(cols/32) * 4 bytes) to the device. */
+int rqa_run_matrix(rqa_handle* h, const uint32_t* host_bits, int64_t rows,
+                   int64_t cols);
+/* The same with the bits in device memory (4-byte aligned), ordered on
+ * cuda_stream. */
+int rqa_run_matrix_device(rqa_handle* h, const uint32_t* dev_bits, int64_t rows,
+                          int64_t cols, void* cuda_stream);
 /* Copy the measures of the last successful run. */
 int rqa_measures(const rqa_handle* h, rqa_measures_t* out);
 
@@ -190,7 +207,8 @@ int rqa_stats(const rqa_handle* h, rqa_stats_t* out);
  * with the same device decision code as the tile kernel (FP32 test with the
  * FP64 recheck band, or FP64).  i, j, out: host arrays of `count` entries;
  * out[q] = R_{i[q], j[q]} (0 or 1).  For spot checks at sizes where the full
- * matrix cannot be enumerated on the CPU. */
+ * matrix cannot be enumerated on the CPU.  RQA_EINVAL after rqa_run_matrix,
+ * whose cells are the caller's. */
 int rqa_sample_decisions(rqa_handle* h, const int64_t* i, const int64_t* j,
                          int64_t count, uint8_t* out);
 

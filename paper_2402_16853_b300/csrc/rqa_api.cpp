@@ -102,6 +102,18 @@ int rqa_create(const rqa_settings* settings, rqa_handle** out) {
   return RQA_OK;
 }
 
+static int run_input(rqa_handle* h, std::vector<rqa::SeriesInput>& in, void* stream) {
+  std::vector<rqa::SeriesResult> res;
+  int rc = h->eng->run(in, res, static_cast<cudaStream_t>(stream), false);
+  if (rc != RQA_OK) {
+    h->err = h->eng->error();
+    return rc;
+  }
+  h->res = std::move(res[0]);
+  h->have = true;
+  return RQA_OK;
+}
+
 static int run_common(rqa_handle* h, const double* host, const double* dev, int64_t n,
                       void* stream, bool cross = false, const double* host2 = nullptr,
                       const double* dev2 = nullptr, int64_t n2 = 0) {
@@ -121,15 +133,27 @@ static int run_common(rqa_handle* h, const double* host, const double* dev, int6
   in[0].host2 = host2;
   in[0].dev2 = dev2;
   in[0].N2 = n2;
-  std::vector<rqa::SeriesResult> res;
-  int rc = h->eng->run(in, res, static_cast<cudaStream_t>(stream), false);
-  if (rc != RQA_OK) {
-    h->err = h->eng->error();
-    return rc;
+  return run_input(h, in, stream);
+}
+
+static int run_matrix(rqa_handle* h, const uint32_t* host_bits, const uint32_t* dev_bits,
+                      int64_t rows, int64_t cols, void* stream) {
+  if (!h) return RQA_EINVAL;
+  h->have = false;
+  h->err.clear();
+  if (!host_bits && !dev_bits) {
+    h->err = "matrix pointer is NULL";
+    return RQA_EINVAL;
   }
-  h->res = std::move(res[0]);
-  h->have = true;
-  return RQA_OK;
+  std::vector<rqa::SeriesInput> in(1);
+  in[0].st = h->st;
+  in[0].matrix = true;
+  in[0].cross = true;
+  in[0].bits_host = host_bits;
+  in[0].bits_dev = dev_bits;
+  in[0].N = rows;
+  in[0].N2 = cols;
+  return run_input(h, in, stream);
 }
 
 int rqa_run(rqa_handle* h, const double* host_series, int64_t n) {
@@ -148,6 +172,15 @@ int rqa_run_cross(rqa_handle* h, const double* host_x, int64_t n_x, const double
 int rqa_run_cross_device(rqa_handle* h, const double* dev_x, int64_t n_x, const double* dev_y,
                          int64_t n_y, void* cuda_stream) {
   return run_common(h, nullptr, dev_x, n_x, cuda_stream, true, nullptr, dev_y, n_y);
+}
+
+int rqa_run_matrix(rqa_handle* h, const uint32_t* host_bits, int64_t rows, int64_t cols) {
+  return run_matrix(h, host_bits, nullptr, rows, cols, nullptr);
+}
+
+int rqa_run_matrix_device(rqa_handle* h, const uint32_t* dev_bits, int64_t rows, int64_t cols,
+                          void* cuda_stream) {
+  return run_matrix(h, nullptr, dev_bits, rows, cols, cuda_stream);
 }
 
 int rqa_measures(const rqa_handle* h, rqa_measures_t* out) {

@@ -40,27 +40,29 @@ int64_t cross_cell_count(int64_t n1, int64_t n2, int64_t w) {
 }
 
 struct Sizes {
-  int64_t n = 0, n2 = 0, hl = 0, nstrips = 0, ndesc = 0;
+  int64_t n = 0, n2 = 0, hl = 0, nstrips = 0, ndesc = 0, wpr = 0;
   int mp = 0;
   TileConfig tc{1, 4};
-  bool f64 = false, cross = false;
+  bool f64 = false, cross = false, matrix = false;
   size_t hist = 0, ends = 0, cnt = 0, desc = 0, series = 0, series2 = 0, xe = 0, xe2 = 0;
 };
 
-// Device buffers of one series (RQA) or one pair of series (cross
-// recurrence: rows from the N values, columns from the N2 values).
+// Device buffers of one series (RQA), one pair of series (cross
+// recurrence: rows from the N values, columns from the N2 values) or one
+// precomputed N x N2 bit matrix (its copy counted in `series`).
 Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross = false,
-                int64_t N2 = 0, bool copy_series2 = false) {
+                int64_t N2 = 0, bool copy_series2 = false, bool matrix = false) {
   Sizes z;
-  z.n = nvec_of(st, N);
-  z.cross = cross;
-  z.n2 = cross ? nvec_of(st, N2) : z.n;
+  z.matrix = matrix;
+  z.n = matrix ? N : nvec_of(st, N);
+  z.cross = cross || matrix;
+  z.n2 = matrix ? N2 : cross ? nvec_of(st, N2) : z.n;
   z.hl = std::max(z.n, z.n2);
-  z.f64 = st.precision == RQA_PREC_FP64;
-  z.mp = z.f64 ? 0 : ((st.m + 3) / 4) * 4;
+  z.f64 = !matrix && st.precision == RQA_PREC_FP64;
+  z.mp = (z.f64 || matrix) ? 0 : ((st.m + 3) / 4) * 4;
   z.tc = choose_tile(z.n2, st.m, st.norm);
   const int64_t sw = 32LL * z.tc.warps * z.tc.cols;
-  if (cross) {
+  if (z.cross) {
     z.nstrips = cross_num_strips(z.n2, sw);
     z.ndesc = z.nstrips * cross_strip_diags(z.n, sw);
   } else {
@@ -68,10 +70,15 @@ Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross 
     z.ndesc = strip_offset(z.n, sw, z.nstrips);
   }
   z.hist = align256(sizeof(uint64_t) * 3 * static_cast<size_t>(z.hl + 1));
-  z.ends = cross ? 0 : align256(sizeof(uint32_t) * 2 * static_cast<size_t>(z.n));
+  z.ends = z.cross ? 0 : align256(sizeof(uint32_t) * 2 * static_cast<size_t>(z.n));
   z.cnt = align256(sizeof(uint64_t) * CNT_WORDS);
-  // RQA: row_a, row_z, dia_a, dia_z; cross recurrence: dia_a, dia_z
-  z.desc = (cross ? 2 : 4) * align256(sizeof(uint16_t) * static_cast<size_t>(z.ndesc));
+  // RQA: row_a, row_z, dia_a, dia_z; cross recurrence and matrices: dia_a, dia_z
+  z.desc = (z.cross ? 2 : 4) * align256(sizeof(uint16_t) * static_cast<size_t>(z.ndesc));
+  if (matrix) {
+    z.wpr = (z.n2 + 31) / 32;
+    z.series = copy_series ? align256(sizeof(uint32_t) * static_cast<size_t>(z.n * z.wpr)) : 0;
+    return z;
+  }
   z.series = copy_series ? align256(sizeof(double) * static_cast<size_t>(N)) : 0;
   z.series2 = cross && copy_series2 ? align256(sizeof(double) * static_cast<size_t>(N2)) : 0;
   z.xe = align256(sizeof(float) * static_cast<size_t>(z.n) * z.mp);
@@ -258,23 +265,40 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   for (int q = 0; q < count; ++q) {
     std::string msg;
     int s = validate_settings(&in[q].st, &msg);
-    if (s == RQA_OK && !in[q].host && !in[q].dev) {
+    if (in[q].matrix) {  // a precomputed matrix: N rows, N2 columns
+      if (s == RQA_OK && !in[q].bits_host && !in[q].bits_dev) {
+        s = RQA_EINVAL;
+        msg = "matrix pointer is NULL";
+      } else if (s == RQA_OK && (in[q].N < 1 || in[q].N2 < 1)) {
+        s = RQA_ESHORT;
+        msg = "matrix has no rows or no columns";
+      } else if (s == RQA_OK && (in[q].N > RQA_MAX_N || in[q].N2 > RQA_MAX_N)) {
+        s = RQA_ETOOBIG;
+        msg = "more than RQA_MAX_N rows or columns";
+      }
+      if (s != RQA_OK) {
+        results[q].status = s;
+        if (count == 1) return fail(s, msg);
+        continue;
+      }
+    }
+    if (!in[q].matrix && s == RQA_OK && !in[q].host && !in[q].dev) {
       s = RQA_EINVAL;
       msg = "series pointer is NULL";
     }
-    if (s == RQA_OK && in[q].N < 1) {
+    if (!in[q].matrix && s == RQA_OK && in[q].N < 1) {
       s = RQA_ESHORT;
       msg = "series is empty";
     }
-    if (s == RQA_OK && nvec_of(in[q].st, in[q].N) < 1) {
+    if (!in[q].matrix && s == RQA_OK && nvec_of(in[q].st, in[q].N) < 1) {
       s = RQA_ESHORT;
       msg = "series shorter than the embedding window (m-1)*tau + 1";
     }
-    if (s == RQA_OK && nvec_of(in[q].st, in[q].N) > RQA_MAX_N) {
+    if (!in[q].matrix && s == RQA_OK && nvec_of(in[q].st, in[q].N) > RQA_MAX_N) {
       s = RQA_ETOOBIG;
       msg = "more than RQA_MAX_N embedded vectors";
     }
-    if (s == RQA_OK && in[q].cross) {
+    if (!in[q].matrix && s == RQA_OK && in[q].cross) {
       if (!in[q].host2 && !in[q].dev2) {
         s = RQA_EINVAL;
         msg = "second series pointer is NULL";
@@ -292,12 +316,18 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       continue;
     }
     P& p = plan[q];
-    p.z = sizes_for(in[q].st, in[q].N, in[q].dev == nullptr, in[q].cross, in[q].N2,
-                    in[q].dev2 == nullptr);
+    if (in[q].matrix)
+      p.z = sizes_for(in[q].st, in[q].N, in[q].bits_dev == nullptr, true, in[q].N2, false, true);
+    else
+      p.z = sizes_for(in[q].st, in[q].N, in[q].dev == nullptr, in[q].cross, in[q].N2,
+                      in[q].dev2 == nullptr);
     p.run = true;
     dev_idx[q] = nrun++;
     (p.z.cross ? any_cross : any_sym) = true;
-    const Key k{in[q].st.m, in[q].st.norm, p.z.f64 ? 1 : 0, p.z.tc.warps, p.z.cross ? 1 : 0};
+    // kernel class: (m, norm, f64, warps, kind), kind 0 RQA, 1 cross, 2 matrix
+    const Key k = p.z.matrix ? Key{0, 0, 0, p.z.tc.warps, 2}
+                             : Key{in[q].st.m, in[q].st.norm, p.z.f64 ? 1 : 0, p.z.tc.warps,
+                                   p.z.cross ? 1 : 0};
     auto it = cls_of.find(k);
     if (it == cls_of.end()) {
       it = cls_of.emplace(k, static_cast<int>(classes.size())).first;
@@ -305,7 +335,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     }
     p.cls = it->second;
     max_n = std::max(max_n, p.z.cross ? p.z.n + p.z.n2 : p.z.n);
-    if (!p.z.f64) {
+    if (!p.z.f64 && !p.z.matrix) {
       any_fp32 = true;
       max_n_mp = std::max(max_n_mp, (p.z.n + (p.z.cross ? p.z.n2 : 0)) * p.z.mp);
     }
@@ -394,18 +424,32 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     if (!p.run) continue;
     const rqa_settings& s = in[q].st;
     SeriesDesc& d = hsd[dev_idx[q]];
-    if (in[q].dev) {
+    if (p.z.matrix) {
+      if (in[q].bits_dev) {
+        d.bits = in[q].bits_dev;
+      } else {
+        d.bits = reinterpret_cast<const uint32_t*>(arena_ + p.o_series);
+        std::memcpy(host_ + h_series + (p.o_series - o_series0), in[q].bits_host,
+                    sizeof(uint32_t) * static_cast<size_t>(p.z.n * p.z.wpr));
+      }
+      d.wpr = p.z.wpr;
+    } else if (in[q].dev) {
       d.s = in[q].dev;
     } else {
       d.s = reinterpret_cast<const double*>(arena_ + p.o_series);
       std::memcpy(host_ + h_series + (p.o_series - o_series0), in[q].host,
                   sizeof(double) * static_cast<size_t>(in[q].N));
     }
-    d.xe = p.z.f64 ? nullptr : reinterpret_cast<float*>(arena_ + p.o_xe);
+    d.xe = (p.z.f64 || p.z.matrix) ? nullptr : reinterpret_cast<float*>(arena_ + p.o_xe);
     d.N = in[q].N;
     d.n = p.z.n;
     desc_set_symmetric(d);
-    if (p.z.cross) {
+    if (p.z.matrix) {
+      d.N2 = in[q].N2;
+      d.n2 = p.z.n2;
+      d.hl = p.z.hl;
+      d.cross = 1;
+    } else if (p.z.cross) {
       if (in[q].dev2) {
         d.s2 = in[q].dev2;
       } else {
@@ -487,6 +531,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       key.push_back(in[q].st.precision);
       key.push_back(in[q].st.tau);
       key.push_back(in[q].cross ? 1 : 0);
+      key.push_back(in[q].matrix ? 1 : 0);
+      key.push_back(reinterpret_cast<int64_t>(in[q].bits_dev));
       key.push_back(in[q].N2);
       key.push_back(reinterpret_cast<int64_t>(in[q].dev2));
     }
@@ -520,10 +566,10 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       const int m = std::get<0>(classes[c]), norm = std::get<1>(classes[c]);
       const bool f64 = std::get<2>(classes[c]) != 0;
       const int warps = std::get<3>(classes[c]);
-      const bool cross = std::get<4>(classes[c]) != 0;
-      TileFn fn = tile_kernel_for(m, norm, 4, f64, cross);
+      const int kind = std::get<4>(classes[c]);
+      TileFn fn = kind == 2 ? tile_kernel_matrix(4) : tile_kernel_for(m, norm, 4, f64, kind == 1);
       if (!fn) return fail(RQA_EINVAL, "no tile kernel for this (m, norm)");
-      const size_t smem = tile_smem_for(m, norm, f64, warps, 4);
+      const size_t smem = tile_smem_for(kind == 2 ? 1 : m, norm, f64, warps, 4);
       if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem))) != cudaSuccess)
@@ -595,6 +641,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   cudaEventElapsedTime(&total_ms_, ev_[0], ev_[3]);
   last_sd_ = d_sd;
   last_f64_ = plan[0].run && plan[0].z.f64;
+  last_matrix_ = plan[0].run && plan[0].z.matrix;
   last_stream_ = st;
 
   // ---- results
@@ -628,14 +675,14 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     rqa_stats_t& s = r.stats;
     s.n_vec = p.z.n;
     s.n_cols = p.z.n2;
-    s.cross = p.z.cross ? 1 : 0;
+    s.mode = p.z.matrix ? 2 : p.z.cross ? 1 : 0;
     s.pairs = p.z.cross ? cross_cell_count(p.z.n, p.z.n2, std::min<int64_t>(in[q].st.theiler, p.z.hl))
                         : pair_count(p.z.n, in[q].st.theiler);
     s.rechecks = static_cast<int64_t>(cnt[CNT_RECHECKS]);
-    s.precision_used = p.z.f64 ? RQA_PREC_FP64 : RQA_PREC_FP32_RECHECK;
+    s.precision_used = p.z.matrix ? RQA_PREC_AUTO : p.z.f64 ? RQA_PREC_FP64 : RQA_PREC_FP32_RECHECK;
     s.band = p.z.f64 ? 0.0 : d.band_rel;
     s.band_bound = p.z.f64 ? 0.0 : d.bound_rel;
-    s.exact = (p.z.f64 || d.band_rel >= d.bound_rel) ? 1 : 0;
+    s.exact = (p.z.f64 || p.z.matrix || d.band_rel >= d.bound_rel) ? 1 : 0;
     s.strip_width = 32 * p.z.tc.warps * p.z.tc.cols;
     s.warps_per_cta = p.z.tc.warps;
     s.cols_per_lane = p.z.tc.cols;
@@ -651,6 +698,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
 
 int Engine::sample(const int64_t* i, const int64_t* j, int64_t count, uint8_t* out) {
   if (!last_sd_) return fail(RQA_EINVAL, "no run to sample from");
+  if (last_matrix_) return fail(RQA_EINVAL, "a precomputed matrix has no decisions to sample");
   if (count <= 0) return RQA_OK;
   cudaError_t e = cudaSetDevice(dev_);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");

@@ -24,6 +24,11 @@ struct SeriesInput {
   const double* host2 = nullptr;
   const double* dev2 = nullptr;
   int64_t N2 = 0;
+  // precomputed matrix (Sect. 9): N rows x N2 columns of bits, row-major,
+  // ceil(N2 / 32) words per row, host or device (cross is set as well)
+  bool matrix = false;
+  const uint32_t* bits_host = nullptr;
+  const uint32_t* bits_dev = nullptr;
 };
 
 struct SeriesResult {
@@ -69,7 +74,8 @@ class Engine {
   int run(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& results,
           cudaStream_t stream, bool use_graph);
 
-  // Decisions R_ij of series 0 of the last run (needs its buffers alive).
+  // Decisions R_ij of series 0 of the last run (needs its buffers alive;
+  // RQA_EINVAL after a precomputed-matrix run, which has no decisions).
   int sample(const int64_t* i, const int64_t* j, int64_t count, uint8_t* out);
 
   const std::string& error() const { return err_; }
@@ -98,6 +104,7 @@ class Engine {
   // last run, for sample()
   SeriesDesc* last_sd_ = nullptr;
   bool last_f64_ = false;
+  bool last_matrix_ = false;
   cudaStream_t last_stream_ = nullptr;
   // graph cache (batched runs with an unchanged plan)
   cudaGraphExec_t graph_ = nullptr;

@@ -24,6 +24,10 @@ struct SeriesDesc {
   int64_t N2, n2;       // its length and vector count; == N, n for RQA
   int64_t hl;           // longest possible line: n (RQA) or max(n, n2)
   int32_t cross;        // 1: rows from s, columns from s2, no symmetry
+  // ---- precomputed matrix (Sect. 9): rows x n2 bits, row-major, bit b of
+  // word w of a row is column 32 w + b; s, s2, xe, xe2 are unused
+  const uint32_t* bits;
+  int64_t wpr;          // words per row, ceil(n2 / 32)
   // ---- filled by the prepare kernel
   double center, scale; // x32 = fl32((s - center) * scale)
   float thr;            // FP32 threshold: eps*scale (L1, max) or its square (L2)

@@ -22,6 +22,8 @@ TileFn tile_kernel_norm2(int m, int cols, bool f64);
 TileFn tile_kernel_cross_norm0(int m, int cols, bool f64);
 TileFn tile_kernel_cross_norm1(int m, int cols, bool f64);
 TileFn tile_kernel_cross_norm2(int m, int cols, bool f64);
+// Line detection over a precomputed bit matrix (no distances).
+TileFn tile_kernel_matrix(int cols);
 
 void launch_prepare(SeriesDesc* d_sd, int count, cudaStream_t st);
 void launch_embed(SeriesDesc* d_sd, int count, int64_t max_n_mp, int sms, cudaStream_t st);

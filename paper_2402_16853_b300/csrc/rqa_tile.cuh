@@ -451,7 +451,7 @@ inline size_t tile_smem_bytes(int warps, int row_elems, int elem_bytes, int cols
 }
 
 // ------------------------------------------------------------------ kernel
-template <int M, int NORM, int C, bool F64, bool XR>
+template <int M, int NORM, int C, bool F64, bool XR, bool MX = false>
 __global__ void __launch_bounds__(256, 3)
 tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, int nitems,
             int* __restrict__ queue) {
@@ -549,7 +549,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
       for (int c = 0; c < C; ++c) {
         const int j = jw0 + 32 * c + lane;
 #pragma unroll
-        for (int k = 0; k < M; ++k) {
+        for (int k = 0; k < (MX ? 0 : M); ++k) {
           if constexpr (F64) {
             xc[c][k] = j >= 0 ? sser2[j + k * tau] : 0.0;
           } else if constexpr (PACKED) {
@@ -574,7 +574,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
 
       for (int b = bhi; b >= 0 && ok; --b) {
         const int r0 = b << 5;
-        {  // row vectors of rows r0 .. r0+31 into this warp's buffer
+        if constexpr (!MX) {  // row vectors of rows r0 .. r0+31 into this warp's buffer
           const int i = r0 + lane;
 #pragma unroll
           for (int k = 0; k < RE; ++k) {
@@ -592,7 +592,33 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
         __syncwarp();
 
         // ---- operator I: recurrence words (bit t = row r0 + t) per column
-        if constexpr (!F64) {
+        if constexpr (MX) {
+          // precomputed matrix: lane l reads row r0 + l's 32 cells of columns
+          // col0 .. col0+31 (two words and a funnel shift when col0 is not a
+          // word boundary; col0 < 0 only in a ragged last strip), and the
+          // warp transpose turns the 32 row words into column words
+          const uint32_t* __restrict__ bits = Sp->bits;
+          const int64_t wpr = Sp->wpr;
+          const int i = r0 + lane;
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            const int col0 = jw0 + 32 * c;
+            uint32_t rw = 0;
+            if (i < n && col0 > -32) {
+              const uint32_t* rowp = bits + (int64_t)i * wpr;
+              if (col0 >= 0) {
+                const int wi = col0 >> 5, sh = col0 & 31;
+                const uint32_t lo = rowp[wi];
+                const uint32_t hi = (sh != 0 && wi + 1 < wpr) ? rowp[wi + 1] : 0u;
+                rw = __funnelshift_r(lo, hi, sh);
+              } else {
+                rw = rowp[0] << (-col0);
+              }
+            }
+            Rw_s[c * 32 + lane] =
+                transpose32(rw, lane) & live_mask<true>(col0 + lane, r0, n, wtheiler);
+          }
+        } else if constexpr (!F64) {
           uint32_t Nw[C];
           float mn[C];
 #pragma unroll

@@ -79,7 +79,7 @@ class _CStats(ctypes.Structure):
                 ("ctas", ctypes.c_int32), ("kernel_ms", ctypes.c_float),
                 ("total_ms", ctypes.c_float), ("h2d_bytes", ctypes.c_int64),
                 ("d2h_bytes", ctypes.c_int64), ("launches", ctypes.c_int32),
-                ("cross", ctypes.c_int32), ("n_cols", ctypes.c_int64)]
+                ("mode", ctypes.c_int32), ("n_cols", ctypes.c_int64)]
 
 
 MEASURE_FIELDS = list(_MEAS_D + _MEAS_I)
@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH):
         "rqa_run_device": (c.c_int, [vp, vp, c.c_int64, vp]),
         "rqa_run_cross": (c.c_int, [vp, P(c.c_double), c.c_int64, P(c.c_double), c.c_int64]),
         "rqa_run_cross_device": (c.c_int, [vp, vp, c.c_int64, vp, c.c_int64, vp]),
+        "rqa_run_matrix": (c.c_int, [vp, P(c.c_uint32), c.c_int64, c.c_int64]),
+        "rqa_run_matrix_device": (c.c_int, [vp, vp, c.c_int64, c.c_int64, vp]),
         "rqa_measures": (c.c_int, [vp, P(_CMeasures)]),
         "rqa_histogram": (c.c_int, [vp, c.c_int32, P(c.c_uint64), c.c_int64, P(c.c_int64)]),
         "rqa_stats": (c.c_int, [vp, P(_CStats)]),
@@ -244,6 +246,39 @@ class RQA:
                                    len(b))
             self._keep = (a, b)
         self._check(rc, "rqa_run_cross")
+        self.n = self.stats()["n_vec"]
+        return self.measures()
+
+    def run_matrix(self, matrix, cols: Optional[int] = None, stream=None) -> dict:
+        """Lines and measures of a precomputed binary matrix: a 2-D array of
+        0/1 (packed here), or packed uint32 words of shape (rows,
+        ceil(cols/32)) with `cols` given -- a host array or a CUDA tensor
+        (int32 / uint32 words, used in place).  Returns the measures."""
+        lib = load()
+        if hasattr(matrix, "is_cuda") and matrix.is_cuda:
+            import torch
+            if cols is None or matrix.dim() != 2 or matrix.element_size() != 4:
+                raise TypeError("a device matrix must be packed 32-bit words with cols given")
+            t = matrix.contiguous()
+            if t.shape[1] != (cols + 31) // 32:
+                raise ValueError("words per row must be ceil(cols / 32)")
+            if stream is None:
+                stream = torch.cuda.current_stream(t.device)
+            sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+            rc = lib.rqa_run_matrix_device(self._h, ctypes.c_void_p(t.data_ptr()), t.shape[0],
+                                           cols, ctypes.c_void_p(sp))
+            self._keep = t
+        else:
+            words = pack_matrix(matrix) if cols is None else np.ascontiguousarray(matrix,
+                                                                                    np.uint32)
+            if cols is None:
+                cols = np.asarray(matrix).shape[1]
+            if words.ndim != 2 or words.shape[1] != (cols + 31) // 32:
+                raise ValueError("words per row must be ceil(cols / 32)")
+            rc = lib.rqa_run_matrix(self._h, words.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                    words.shape[0], cols)
+            self._keep = words
+        self._check(rc, "rqa_run_matrix")
         self.n = self.stats()["n_vec"]
         return self.measures()
 
@@ -435,6 +470,20 @@ def cross_recurrence_plot(settings: Settings, x, y, i0: int = 0, j0: int = 0,
         return out
     bits = np.unpackbits(out.view(np.uint8), axis=1, bitorder="little")
     return bits[:, :cols]
+
+
+def pack_matrix(matrix) -> np.ndarray:
+    """Pack a 2-D 0/1 array into the library's bit layout: (rows,
+    ceil(cols/32)) uint32 words, bit b of word w = column 32 w + b."""
+    a = np.asarray(matrix) != 0
+    if a.ndim != 2:
+        raise ValueError("matrix must be two-dimensional")
+    rows, cols = a.shape
+    wpr = (cols + 31) // 32
+    padded = np.zeros((rows, wpr * 32), dtype=bool)
+    padded[:, :cols] = a
+    b = np.packbits(padded, axis=1, bitorder="little")
+    return np.ascontiguousarray(b).view(np.uint32).reshape(rows, wpr)
 
 
 def write_pgm(path: str, plot) -> None:

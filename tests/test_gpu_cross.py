@@ -36,7 +36,7 @@ def check_cross(x, y, **kw):
     assert np.array_equal(hw, want["hw"]), _diff("white", hw, want["hw"])
     assert_same_measures(meas, want["measures"])
     st = r.stats()
-    assert st["cross"] == 1 and st["n_vec"] == want["n"] and st["n_cols"] == want["cols"]
+    assert st["mode"] == 1 and st["n_vec"] == want["n"] and st["n_cols"] == want["cols"]
     return r, st, want
 
 
