@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cross", action="store_true")
     ap.add_argument("--no-sine", action="store_true")
+    ap.add_argument("--no-matrix", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--N", type=int, default=0,
@@ -320,6 +321,11 @@ def run_mine(args):
     if not args.no_cross:
         extra["cross"] = bench_cross(gp, params, dev, barrier, flush, peak)
 
+    # ---- line detection over a precomputed bit matrix, and the plot (context)
+    if not args.no_matrix:
+        extra["matrix_input"] = bench_matrix(gp, dev, barrier, flush)
+        extra["plot"] = bench_plot(gp, s, params)
+
     # ---- the paper's own timing workload (context line)
     if not args.no_sine:
         extra["paper_sine"] = bench_sine(gp, dev, barrier)
@@ -397,6 +403,51 @@ def bench_cross(gp, params, dev, barrier, flush, peak, N=524_288, steps=2):
             "kernel_ms": k_ms, "roofline_frac": achieved / peak,
             "kernel": f"tile_kernel<{params['m']},L2,4,fp32,cross>",
             "rechecks": int(st["rechecks"]), "rr": r.measures()["rr"]}
+
+
+def bench_matrix(gp, dev, barrier, flush, rows=32768, cols=32768, steps=3):
+    """rqa_run_matrix_device on a random bit matrix (each bit the AND of
+    three random bits: density 1/8, seed 5) with a black band of columns
+    5,024 .. 5,311 across strips: rows x cols cells per step."""
+    import torch
+    rng = np.random.default_rng(5)
+    wpr = (cols + 31) // 32
+    words = rng.integers(0, 1 << 32, size=(rows, wpr), dtype=np.uint32)
+    for _ in range(2):
+        words &= rng.integers(0, 1 << 32, size=(rows, wpr), dtype=np.uint32)
+    words[:, 157:166] = 0xFFFFFFFF
+    t = torch.from_numpy(words.view(np.int32)).to(dev)
+    r = gp.RQA(gp.Settings(m=1, tau=1, eps=1.0, norm=0, theiler=0))
+    r.run_matrix(t, cols=cols)
+    barrier()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    kms = []
+    e0.record(stream)
+    for _ in range(steps):
+        flush.fill_(1)
+        r.run_matrix(t, cols=cols)
+        kms.append(r.stats()["kernel_ms"])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sec = e0.elapsed_time(e1) / 1e3 / steps
+    return {"workload": f"{rows} x {cols} random bit matrix (density 1/8) on the device",
+            "value": float(rows) * cols / sec, "unit": "cells/s", "ms_per_step": sec * 1e3,
+            "kernel_ms": float(np.mean(kms)), "matrix_bytes": int(words.nbytes),
+            "rr": r.measures()["rr"]}
+
+
+def bench_plot(gp, s, params, rows=8192, cols=8192):
+    """rqa_recurrence_plot: an 8,192 x 8,192 window of the primary series'
+    matrix, bit-packed, to host memory (one call, wall clock)."""
+    st = gp.Settings(**params)
+    gp.recurrence_plot(st, s, i0=0, j0=0, rows=64, cols=64)
+    t0 = time.perf_counter()
+    gp.recurrence_plot(st, s, i0=500_000, j0=500_000, rows=rows, cols=cols, packed=True)
+    sec = time.perf_counter() - t0
+    return {"workload": f"{rows} x {cols} window of the primary series' matrix",
+            "value": float(rows) * cols / sec, "unit": "cells/s", "seconds": sec}
 
 
 def bench_sine(gp, dev, barrier, steps=2):

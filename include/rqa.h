@@ -268,6 +268,26 @@ int rqa_cross_recurrence_plot(const rqa_settings* settings, const double* host_x
                               uint32_t* out_bits);
 const char* rqa_plot_last_error(void);
 
+/* --------------------------------------------------------------- autotuner
+ * Sect. 9 plans the automatic selection of the best-performing
+ * implementation at runtime.  rqa_autotune() times whole runs (device time
+ * from the first copy to the last) for each CTA-strip width (1, 2, 4 and 8 warps; 128 columns per warp) on one series
+ * -- host_series of n_points values, or a built-in z-scored AR(1) series of
+ * n_points values when host_series is NULL -- as RQA (cross = 0) or as the
+ * cross recurrence of the series with itself (cross = 1), and records the
+ * fastest width for the class (RQA or cross, m, norm, FP64 or not,
+ * ceil(log2 n)).  Every later run of that class in the process (single,
+ * cross, batched, served) uses the recorded width; results do not depend on
+ * it.  *best_warps receives the width; ms_per_width (4 floats, may be NULL)
+ * the best of two timed runs per width.  rqa_autotune_clear() forgets every
+ * recorded width.  The environment variable RQA_TILE_WARPS (1..8) overrides
+ * the table.  rqa_autotune_last_error() describes the last failure of the
+ * calling thread. */
+int rqa_autotune(const rqa_settings* settings, const double* host_series,
+                 int64_t n_points, int32_t cross, int32_t* best_warps,
+                 float* ms_per_width);
+void rqa_autotune_clear(void);
+const char* rqa_autotune_last_error(void);
 /* ----------------------------------------------------------------- batched
  * Many independent series in one submission: the work of all series is one
  * queue of (series, strip) items processed by persistent CTAs, one launch

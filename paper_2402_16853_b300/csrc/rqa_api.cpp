@@ -56,7 +56,8 @@ int copy_hist(const rqa::SeriesResult& r, int32_t kind, uint64_t* out, int64_t c
   const int64_t need = r.hl + 1;
   if (len) *len = need;
   if (!out || cap < need) return RQA_EINVAL;
-  std::memcpy(out, r.hist.data() + kind * need, sizeof(uint64_t) * need);
+  if (!r.hist) return RQA_EINVAL;
+  std::memcpy(out, r.hist + kind * need, sizeof(uint64_t) * need);
   return RQA_OK;
 }
 

@@ -2,10 +2,14 @@
 #include "rqa_engine.h"
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <thread>
 #include <tuple>
 
 #include "rqa_kernels.h"
@@ -15,6 +19,43 @@ namespace rqa {
 namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+// f(q) for q in [0, count) on up to 16 host threads, at least `per_thread`
+// items each (serially when that leaves one thread).
+template <class F>
+void parallel_for(int count, int per_thread, F&& f) {
+  const int hw = static_cast<int>(std::thread::hardware_concurrency());
+  const int T = std::min({16, std::max(hw, 1), count / std::max(per_thread, 1)});
+  if (T <= 1) {
+    for (int q = 0; q < count; ++q) f(q);
+    return;
+  }
+  std::atomic<int> next{0};
+  std::vector<std::thread> th;
+  th.reserve(T);
+  for (int t = 0; t < T; ++t)
+    th.emplace_back([&] {
+      for (int q; (q = next.fetch_add(1)) < count;) f(q);
+    });
+  for (auto& x : th) x.join();
+}
+
+// RQA_TRACE=1: one line per run on stderr with the host phases of the run
+// (plan, staging, enqueue, wait for the device, results) and the device
+// times, for finding where a call spends its time.
+bool trace_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("RQA_TRACE");
+    return e && *e && *e != '0';
+  }();
+  return on;
+}
+
+struct HostCopy {
+  void* dst;
+  const void* src;
+  size_t bytes;
+};
 
 int64_t nvec_of(const rqa_settings& st, int64_t N) {
   return N - static_cast<int64_t>(st.m - 1) * st.tau;
@@ -51,7 +92,8 @@ struct Sizes {
 // recurrence: rows from the N values, columns from the N2 values) or one
 // precomputed N x N2 bit matrix (its copy counted in `series`).
 Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross = false,
-                int64_t N2 = 0, bool copy_series2 = false, bool matrix = false) {
+                int64_t N2 = 0, bool copy_series2 = false, bool matrix = false,
+                int warps = 0) {
   Sizes z;
   z.matrix = matrix;
   z.n = matrix ? N : nvec_of(st, N);
@@ -60,7 +102,8 @@ Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross 
   z.hl = std::max(z.n, z.n2);
   z.f64 = !matrix && st.precision == RQA_PREC_FP64;
   z.mp = (z.f64 || matrix) ? 0 : ((st.m + 3) / 4) * 4;
-  z.tc = choose_tile(z.n2, st.m, st.norm);
+  z.tc = choose_tile(z.n2, st.m, st.norm, z.f64, matrix ? 2 : cross ? 1 : 0);
+  if (warps > 0) z.tc.warps = warps;
   const int64_t sw = 32LL * z.tc.warps * z.tc.cols;
   if (z.cross) {
     z.nstrips = cross_num_strips(z.n2, sw);
@@ -132,9 +175,7 @@ int validate_settings(const rqa_settings* st, std::string* msg) {
   return RQA_OK;
 }
 
-TileConfig choose_tile(int64_t n, int m, int norm) {
-  (void)m;
-  (void)norm;
+TileConfig choose_tile(int64_t n, int m, int norm, bool f64, int kind) {
   TileConfig c{1, 4};
   if (n >= 65536)
     c.warps = 8;
@@ -142,15 +183,19 @@ TileConfig choose_tile(int64_t n, int m, int norm) {
     c.warps = 4;
   else if (n >= 4096)
     c.warps = 2;
+  if (const int t = tune_lookup(kind, m, norm, f64, n)) c.warps = t;
   if (const char* e = std::getenv("RQA_TILE_WARPS")) {
     const int w = std::atoi(e);
     if (w >= 1 && w <= 8) c.warps = w;
   }
+  if (const int f = tune_forced_warps()) c.warps = f;
   return c;
 }
 
 size_t series_device_bytes(const rqa_settings& st, int64_t N) {
-  const Sizes z = sizes_for(st, N, true);
+  // the narrowest strips (one warp) need the most descriptors: a run that
+  // batches this series with others, or an autotuned width, never needs more
+  const Sizes z = sizes_for(st, N, true, false, 0, false, false, 1);
   return z.hist + z.ends + z.cnt + z.desc + z.series + z.xe + align256(sizeof(SeriesDesc)) +
          align256(sizeof(Item) * static_cast<size_t>(z.nstrips)) + 256;
 }
@@ -160,6 +205,9 @@ Engine::Engine(int device) : dev_(device) {
   cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev_);
   cudaStreamCreateWithFlags(&own_, cudaStreamNonBlocking);
   for (auto& e : ev_) cudaEventCreate(&e);
+  for (auto& a : aux_) cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking);
+  cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming);
+  for (auto& j : join_) cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
 }
 
 Engine::~Engine() {
@@ -167,6 +215,11 @@ Engine::~Engine() {
   if (graph_) cudaGraphExecDestroy(graph_);
   for (auto& e : ev_)
     if (e) cudaEventDestroy(e);
+  for (auto& j : join_)
+    if (j) cudaEventDestroy(j);
+  if (fork_) cudaEventDestroy(fork_);
+  for (auto& a : aux_)
+    if (a) cudaStreamDestroy(a);
   if (own_) cudaStreamDestroy(own_);
   if (arena_) cudaFree(arena_);
   if (host_) cudaFreeHost(host_);
@@ -233,7 +286,7 @@ int Engine::run(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& r
   const int rc = run_impl(in, results, stream, use_graph);
   if (rc != RQA_OK)  // a failure of the whole set marks every unfinished series
     for (auto& r : results)
-      if (r.status == RQA_OK && r.hist.empty()) r.status = rc;
+      if (r.status == RQA_OK && !r.hist) r.status = rc;
   return rc;
 }
 
@@ -247,6 +300,10 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   if (count == 0) return RQA_OK;
   cudaStream_t st = stream ? stream : own_;
 
+  using clk = std::chrono::steady_clock;
+  const bool tracing = trace_enabled();
+  clk::time_point tp[6];
+  tp[0] = clk::now();
   // ---- plan: validation, sizes, kernel classes
   struct P {
     Sizes z;
@@ -315,13 +372,45 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       if (count == 1) return fail(s, msg);
       continue;
     }
+    plan[q].run = true;
+  }
+  // In a set of several series, every series of a kernel group (kind, m,
+  // norm, precision) gets the strip width chosen for the group's widest
+  // matrix, so the group is one persistent launch (measured: 21 launches at
+  // one width each beat 63 launches at per-series widths by 14 % on the
+  // 4,096-series batch).
+  using GroupKey = std::tuple<int, int, int, int>;
+  std::map<GroupKey, int64_t> group_cols;
+  auto group_of = [&](int q) {
+    const rqa_settings& st = in[q].st;
+    if (in[q].matrix) return GroupKey{2, 0, 0, 0};
+    return GroupKey{in[q].cross ? 1 : 0, st.m, st.norm, st.precision == RQA_PREC_FP64 ? 1 : 0};
+  };
+  auto cols_of = [&](int q) {
+    if (in[q].matrix) return in[q].N2;
+    return nvec_of(in[q].st, in[q].cross ? in[q].N2 : in[q].N);
+  };
+  if (count > 1)
+    for (int q = 0; q < count; ++q)
+      if (plan[q].run) {
+        int64_t& g = group_cols[group_of(q)];
+        g = std::max(g, cols_of(q));
+      }
+  for (int q = 0; q < count; ++q) {
     P& p = plan[q];
+    if (!p.run) continue;
+    int warps = 0;
+    if (count > 1) {
+      const GroupKey g = group_of(q);
+      warps = choose_tile(group_cols[g], std::get<1>(g), std::get<2>(g), std::get<3>(g) != 0,
+                          std::get<0>(g)).warps;
+    }
     if (in[q].matrix)
-      p.z = sizes_for(in[q].st, in[q].N, in[q].bits_dev == nullptr, true, in[q].N2, false, true);
+      p.z = sizes_for(in[q].st, in[q].N, in[q].bits_dev == nullptr, true, in[q].N2, false, true,
+                      warps);
     else
       p.z = sizes_for(in[q].st, in[q].N, in[q].dev == nullptr, in[q].cross, in[q].N2,
-                      in[q].dev2 == nullptr);
-    p.run = true;
+                      in[q].dev2 == nullptr, false, warps);
     dev_idx[q] = nrun++;
     (p.z.cross ? any_cross : any_sym) = true;
     // kernel class: (m, norm, f64, warps, kind), kind 0 RQA, 1 cross, 2 matrix
@@ -416,9 +505,11 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   rc = ensure_host(hoff);
   if (rc != RQA_OK) return rc;
 
+  tp[1] = clk::now();
   // ---- fill staging
   SeriesDesc* hsd = reinterpret_cast<SeriesDesc*>(host_ + h_sd);
   std::memset(hsd, 0, sizeof(SeriesDesc) * nrun);
+  std::vector<HostCopy> copies;  // series into the pinned staging, done in parallel below
   for (int q = 0; q < count; ++q) {
     const P& p = plan[q];
     if (!p.run) continue;
@@ -429,16 +520,16 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
         d.bits = in[q].bits_dev;
       } else {
         d.bits = reinterpret_cast<const uint32_t*>(arena_ + p.o_series);
-        std::memcpy(host_ + h_series + (p.o_series - o_series0), in[q].bits_host,
-                    sizeof(uint32_t) * static_cast<size_t>(p.z.n * p.z.wpr));
+        copies.push_back({host_ + h_series + (p.o_series - o_series0), in[q].bits_host,
+                          sizeof(uint32_t) * static_cast<size_t>(p.z.n * p.z.wpr)});
       }
       d.wpr = p.z.wpr;
     } else if (in[q].dev) {
       d.s = in[q].dev;
     } else {
       d.s = reinterpret_cast<const double*>(arena_ + p.o_series);
-      std::memcpy(host_ + h_series + (p.o_series - o_series0), in[q].host,
-                  sizeof(double) * static_cast<size_t>(in[q].N));
+      copies.push_back({host_ + h_series + (p.o_series - o_series0), in[q].host,
+                        sizeof(double) * static_cast<size_t>(in[q].N)});
     }
     d.xe = (p.z.f64 || p.z.matrix) ? nullptr : reinterpret_cast<float*>(arena_ + p.o_xe);
     d.N = in[q].N;
@@ -454,8 +545,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
         d.s2 = in[q].dev2;
       } else {
         d.s2 = reinterpret_cast<const double*>(arena_ + p.o_series2);
-        std::memcpy(host_ + h_series + (p.o_series2 - o_series0), in[q].host2,
-                    sizeof(double) * static_cast<size_t>(in[q].N2));
+        copies.push_back({host_ + h_series + (p.o_series2 - o_series0), in[q].host2,
+                          sizeof(double) * static_cast<size_t>(in[q].N2)});
       }
       d.xe2 = p.z.f64 ? nullptr : reinterpret_cast<float*>(arena_ + p.o_xe2);
       d.N2 = in[q].N2;
@@ -488,6 +579,9 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     }
     d.counters = reinterpret_cast<unsigned long long*>(arena_ + p.o_cnt);
   }
+  parallel_for(static_cast<int>(copies.size()), 8, [&](int k) {
+    std::memcpy(copies[k].dst, copies[k].src, copies[k].bytes);
+  });
   // work items per class, longest strips first
   Item* hitems = reinterpret_cast<Item*>(host_ + h_items);
   std::vector<int64_t> cls_start(ncls + 1, 0);
@@ -511,6 +605,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     cls_start[ncls] = pos;
   }
 
+  tp[2] = clk::now();
   // ---- launch sequence
   SeriesDesc* d_sd = reinterpret_cast<SeriesDesc*>(arena_ + o_sd);
   Item* d_items = reinterpret_cast<Item*>(arena_ + o_items);
@@ -539,13 +634,43 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   }
   const bool replay = use_graph && graph_ && key == graph_key_;
 
+  // Classes run on up to kAux side streams so that small classes overlap
+  // (their CTAs never wait on each other); the longest work goes first, each
+  // class to the least loaded stream.  One class runs on the main stream.
+  std::vector<int> cls_order(ncls), cls_stream(ncls, -1);
+  const int nside = ncls > 1 ? std::min(ncls, kAux) : 0;
+  {
+    std::vector<double> work(ncls, 0.0);
+    for (int q = 0; q < count; ++q) {
+      const P& p = plan[q];
+      if (!p.run) continue;
+      work[p.cls] += static_cast<double>(p.z.n) * static_cast<double>(p.z.n2);
+    }
+    for (int c = 0; c < ncls; ++c) cls_order[c] = c;
+    std::stable_sort(cls_order.begin(), cls_order.end(),
+                     [&](int a, int b) { return work[a] > work[b]; });
+    std::vector<double> load(std::max(nside, 1), 0.0);
+    for (int c : cls_order) {
+      int best = 0;
+      for (int k = 1; k < nside; ++k)
+        if (load[k] < load[best]) best = k;
+      if (nside) {
+        cls_stream[c] = best;
+        load[best] += work[c];
+      }
+    }
+  }
+  // timing events are external nodes when captured, so replays record them
+  const unsigned evflags = use_graph ? cudaEventRecordExternal : cudaEventRecordDefault;
+
   int launches = 0;
   int64_t ctas_total = 0;
   auto enqueue = [&]() -> int {
     cudaError_t e;
     launches = 0;
     ctas_total = 0;
-    if ((e = cudaEventRecord(ev_[0], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaEventRecordWithFlags(ev_[0], st, evflags)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventRecord");
     if ((e = cudaMemsetAsync(arena_ + o_zero, 0, zero_bytes, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemsetAsync");
     if ((e = cudaMemcpyAsync(arena_ + o_sd, host_ + h_sd, (o_zero - o_sd), cudaMemcpyHostToDevice,
@@ -561,8 +686,15 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       launch_embed(d_sd, nrun, max_n_mp, sms_, st);
       ++launches;
     }
-    if ((e = cudaEventRecord(ev_[1], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-    for (int c = 0; c < ncls; ++c) {
+    if ((e = cudaEventRecordWithFlags(ev_[1], st, evflags)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventRecord");
+    if (nside) {
+      if ((e = cudaEventRecord(fork_, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+      for (int k = 0; k < nside; ++k)
+        if ((e = cudaStreamWaitEvent(aux_[k], fork_, 0)) != cudaSuccess)
+          return cuda_fail(e, "cudaStreamWaitEvent");
+    }
+    for (int c : cls_order) {
       const int m = std::get<0>(classes[c]), norm = std::get<1>(classes[c]);
       const bool f64 = std::get<2>(classes[c]) != 0;
       const int warps = std::get<3>(classes[c]);
@@ -587,12 +719,19 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       void* args[] = {&a_sd, &a_items, &a_n, &a_queue};
       if ((e = cudaLaunchKernel(reinterpret_cast<const void*>(fn),
                                 dim3(static_cast<unsigned>(grid)), dim3(32 * warps), args, smem,
-                                st)) != cudaSuccess)
+                                cls_stream[c] >= 0 ? aux_[cls_stream[c]] : st)) != cudaSuccess)
         return cuda_fail(e, "tile kernel launch");
       ++launches;
       ctas_total += grid;
     }
-    if ((e = cudaEventRecord(ev_[2], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    for (int k = 0; k < nside; ++k) {
+      if ((e = cudaEventRecord(join_[k], aux_[k])) != cudaSuccess)
+        return cuda_fail(e, "cudaEventRecord");
+      if ((e = cudaStreamWaitEvent(st, join_[k], 0)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamWaitEvent");
+    }
+    if ((e = cudaEventRecordWithFlags(ev_[2], st, evflags)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventRecord");
     launches += launch_merges(d_sd, nrun, max_n, any_sym, any_cross, sms_, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "merge kernels launch");
     if ((e = cudaMemcpyAsync(host_ + h_hist, arena_ + o_hist0, hist_bytes + cnt_bytes,
@@ -601,7 +740,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     if ((e = cudaMemcpyAsync(host_ + h_sd, arena_ + o_sd, sizeof(SeriesDesc) * nrun,
                              cudaMemcpyDeviceToHost, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync(series state)");
-    if ((e = cudaEventRecord(ev_[3], st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaEventRecordWithFlags(ev_[3], st, evflags)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventRecord");
     return RQA_OK;
   };
 
@@ -635,7 +775,9 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     rc = enqueue();
     if (rc != RQA_OK) return rc;
   }
+  tp[3] = clk::now();
   ce = cudaStreamSynchronize(st);
+  tp[4] = clk::now();
   if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
   cudaEventElapsedTime(&tile_ms_, ev_[1], ev_[2]);
   cudaEventElapsedTime(&total_ms_, ev_[0], ev_[3]);
@@ -644,15 +786,11 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   last_matrix_ = plan[0].run && plan[0].z.matrix;
   last_stream_ = st;
 
-  // ---- results
-  int first_err = RQA_OK;
-  for (int q = 0; q < count; ++q) {
+  // ---- results (per series in parallel: histogram copy and host measures)
+  parallel_for(count, 8, [&](int q) {
     const P& p = plan[q];
     SeriesResult& r = results[q];
-    if (!p.run) {
-      if (first_err == RQA_OK) first_err = r.status;
-      continue;
-    }
+    if (!p.run) return;
     const uint64_t* cnt = reinterpret_cast<const uint64_t*>(host_ + h_cnt + (p.o_cnt - o_cnt0));
     const SeriesDesc& d = hsd[dev_idx[q]];
     r.n = p.z.n;
@@ -662,15 +800,10 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     if (r.status == RQA_OK) {
       const uint64_t* h = reinterpret_cast<const uint64_t*>(host_ + h_hist + (p.o_hist - o_hist0));
       const int64_t L1 = p.z.hl + 1;
-      r.hist.assign(h, h + 3 * L1);
-      measures_from_histograms_rect(r.hist.data(), r.hist.data() + L1, r.hist.data() + 2 * L1,
+      r.hist = h;
+      measures_from_histograms_rect(h, h + L1, h + 2 * L1,
                                     p.z.hl, p.z.n, p.z.n2, in[q].st.l_min, in[q].st.v_min,
                                     in[q].st.w_min, &r.meas);
-    } else if (first_err == RQA_OK) {
-      first_err = r.status;
-      err_ = r.status == RQA_ENAN       ? "series contains NaN or infinite values"
-             : r.status == RQA_ETIMEOUT ? "a bounded device-side wait gave up"
-                                        : "internal error: a line length outside 1..n";
     }
     rqa_stats_t& s = r.stats;
     s.n_vec = p.z.n;
@@ -692,6 +825,27 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     s.d2h_bytes = static_cast<int64_t>(hist_bytes + cnt_bytes + sizeof(SeriesDesc) * nrun);
     s.launches = launches;
     s.ctas = static_cast<int32_t>(ctas_total);
+  });
+  int first_err = RQA_OK;
+  for (int q = 0; q < count && first_err == RQA_OK; ++q) {
+    const SeriesResult& r = results[q];
+    if (r.status == RQA_OK) continue;
+    first_err = r.status;
+    if (plan[q].run)
+      err_ = r.status == RQA_ENAN       ? "series contains NaN or infinite values"
+             : r.status == RQA_ETIMEOUT ? "a bounded device-side wait gave up"
+                                        : "internal error: a line length outside 1..n";
+  }
+  if (tracing) {
+    tp[5] = clk::now();
+    auto ms = [&](int a, int b) {
+      return std::chrono::duration<double, std::milli>(tp[b] - tp[a]).count();
+    };
+    std::fprintf(stderr,
+                 "rqa trace: series=%d classes=%d plan=%.3f staging=%.3f enqueue=%.3f "
+                 "wait=%.3f results=%.3f ms; device total=%.3f tile=%.3f ms%s\n",
+                 count, ncls, ms(0, 1), ms(1, 2), ms(2, 3), ms(3, 4), ms(4, 5), total_ms_,
+                 tile_ms_, use_graph ? (replay ? " (graph replay)" : " (graph capture)") : "");
   }
   return first_err;
 }

@@ -36,7 +36,9 @@ struct SeriesResult {
   int64_t n = 0;               // rows (embedded vectors of the series)
   int64_t n2 = 0;              // columns (== n for RQA)
   int64_t hl = 0;              // histogram length - 1: n, or max(n, n2)
-  std::vector<uint64_t> hist;  // 3 * (hl + 1): diagonal, vertical, white vertical
+  // 3 * (hl + 1) counts: diagonal, vertical, white vertical.  Points into
+  // the engine's pinned staging buffer: valid until the engine's next run.
+  const uint64_t* hist = nullptr;
   rqa_measures_t meas{};
   rqa_stats_t stats{};
 };
@@ -45,11 +47,22 @@ struct SeriesResult {
 // and a message.
 int validate_settings(const rqa_settings* st, std::string* msg);
 
-// Tile configuration for a series of n vectors (warps per CTA strip,
-// columns per lane); may be overridden by RQA_TILE_WARPS for tuning.
-TileConfig choose_tile(int64_t n, int m, int norm);
+// Tile configuration (warps per CTA strip, columns per lane) for a matrix
+// of n columns of kernel kind 0 (RQA), 1 (cross recurrence) or 2 (matrix
+// input): the autotuner's choice for the class (kind, m, norm, f64,
+// ceil(log2 n)) if it recorded one, else a rule by size.  A sweep forced on
+// the calling thread (tune_force_warps) or RQA_TILE_WARPS overrides both.
+TileConfig choose_tile(int64_t n, int m, int norm, bool f64 = false, int kind = 0);
 
-// Device bytes a series of length N needs (for admission control).
+// The autotuner's table (process-wide, thread-safe; rqa_tune.cpp).
+int tune_lookup(int kind, int m, int norm, bool f64, int64_t n);  // 0: none
+void tune_record(int kind, int m, int norm, bool f64, int64_t n, int warps);
+void tune_clear();
+void tune_force_warps(int warps);  // this thread only; 0 ends the override
+int tune_forced_warps();
+
+// Device bytes a series of length N needs at most, whatever strip width
+// runs it (for admission control).
 size_t series_device_bytes(const rqa_settings& st, int64_t N);
 
 void measures_from_histograms(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
@@ -99,6 +112,11 @@ class Engine {
   unsigned char* host_ = nullptr;  // pinned staging
   size_t host_cap_ = 0;
   cudaEvent_t ev_[4] = {nullptr, nullptr, nullptr, nullptr};
+  // side streams: the tile launches of several kernel classes overlap
+  static constexpr int kAux = 4;
+  cudaStream_t aux_[kAux] = {};
+  cudaEvent_t fork_ = nullptr;
+  cudaEvent_t join_[kAux] = {};
   std::string err_;
   float tile_ms_ = 0.f, total_ms_ = 0.f;
   // last run, for sample()

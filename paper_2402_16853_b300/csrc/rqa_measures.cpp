@@ -6,6 +6,8 @@
 // own and the result does not depend on the compiler's choice of FMA.
 #include <cmath>
 #include <cstdint>
+#include <utility>
+#include <vector>
 
 #include "../../include/rqa.h"
 
@@ -13,34 +15,39 @@ namespace rqa {
 
 namespace {
 
-struct Sums {
-  uint64_t count = 0;  // number of lines with length >= lo
-  uint64_t cells = 0;  // sum of their lengths
+// One pass over a histogram: the sums the measures need for lengths >= lo
+// (and the total over all lengths), the longest such length, and the
+// non-zero entries >= lo in ascending order for the entropy.
+struct Scan {
+  uint64_t count = 0;      // lines with length >= lo
+  uint64_t cells = 0;      // sum of their lengths
+  uint64_t cells_all = 0;  // sum of the lengths of all lines
+  int64_t longest = 0;     // longest length >= lo (0 if none)
+  std::vector<std::pair<int64_t, uint64_t>> nz;
 };
 
-Sums sums_from(const uint64_t* h, int64_t n, int64_t lo) {
-  Sums s;
-  for (int64_t l = lo < 1 ? 1 : lo; l <= n; ++l) {
-    s.count += h[l];
-    s.cells += static_cast<uint64_t>(l) * h[l];
+Scan scan(const uint64_t* h, int64_t n, int64_t lo) {
+  Scan s;
+  const int64_t floor_len = lo < 1 ? 1 : lo;
+  for (int64_t l = 1; l <= n; ++l) {
+    const uint64_t v = h[l];
+    if (!v) continue;
+    s.cells_all += static_cast<uint64_t>(l) * v;
+    if (l < floor_len) continue;
+    s.count += v;
+    s.cells += static_cast<uint64_t>(l) * v;
+    s.longest = l;
+    s.nz.emplace_back(l, v);
   }
   return s;
 }
 
-int64_t longest(const uint64_t* h, int64_t n, int64_t lo) {
-  const int64_t floor_len = lo < 1 ? 1 : lo;
-  int64_t l = n;
-  while (l >= floor_len && h[l] == 0) --l;
-  return l >= floor_len ? l : 0;
-}
-
 // Shannon entropy (natural log) of the lengths >= lo, terms in ascending l.
-double entropy(const uint64_t* h, int64_t n, int64_t lo, uint64_t count) {
+double entropy(const Scan& s) {
   double acc = 0.0;
-  const double total = static_cast<double>(count);
-  for (int64_t l = lo < 1 ? 1 : lo; l <= n; ++l) {
-    if (!h[l]) continue;
-    const double p = static_cast<double>(h[l]) / total;
+  const double total = static_cast<double>(s.count);
+  for (const auto& e : s.nz) {
+    const double p = static_cast<double>(e.second) / total;
     const double term = p * std::log(p);
     acc = acc + term;
   }
@@ -62,27 +69,25 @@ void measures_from_histograms(const uint64_t* hd, const uint64_t* hv, const uint
 void measures_from_histograms_rect(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
                                    int64_t n, int64_t rows, int64_t cols, int32_t l_min,
                                    int32_t v_min, int32_t w_min, rqa_measures_t* out) {
-  const Sums d = sums_from(hd, n, l_min), d_all = sums_from(hd, n, 1);
-  const Sums v = sums_from(hv, n, v_min), v_all = sums_from(hv, n, 1);
-  const Sums w = sums_from(hw, n, w_min);
+  const Scan d = scan(hd, n, l_min), v = scan(hv, n, v_min), w = scan(hw, n, w_min);
   // every recurrence point lies on exactly one vertical line
-  const uint64_t rp = v_all.cells;
+  const uint64_t rp = v.cells_all;
   out->n_vec = rows;
   out->recurrence_points = static_cast<int64_t>(rp);
   const double nn = static_cast<double>(rows) * static_cast<double>(cols);
   out->rr = static_cast<double>(rp) / nn;
-  out->det = static_cast<double>(d.cells) / static_cast<double>(d_all.cells);
+  out->det = static_cast<double>(d.cells) / static_cast<double>(d.cells_all);
   out->l = static_cast<double>(d.cells) / static_cast<double>(d.count);
-  out->l_max = longest(hd, n, l_min);
+  out->l_max = d.longest;
   out->div = 1.0 / static_cast<double>(out->l_max);
-  out->l_entr = entropy(hd, n, l_min, d.count);
-  out->lam = static_cast<double>(v.cells) / static_cast<double>(v_all.cells);
+  out->l_entr = entropy(d);
+  out->lam = static_cast<double>(v.cells) / static_cast<double>(v.cells_all);
   out->tt = static_cast<double>(v.cells) / static_cast<double>(v.count);
-  out->v_max = longest(hv, n, v_min);
-  out->v_entr = entropy(hv, n, v_min, v.count);
+  out->v_max = v.longest;
+  out->v_entr = entropy(v);
   out->w = static_cast<double>(w.cells) / static_cast<double>(w.count);
-  out->w_max = longest(hw, n, w_min);
-  out->w_entr = entropy(hw, n, w_min, w.count);
+  out->w_max = w.longest;
+  out->w_entr = entropy(w);
 }
 
 }  // namespace rqa

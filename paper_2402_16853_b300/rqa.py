@@ -134,6 +134,10 @@ def load(path: str = LIB_PATH):
                                                 c.c_int64, c.c_int64, c.c_int64,
                                                 P(c.c_uint32)]),
         "rqa_plot_last_error": (c.c_char_p, []),
+        "rqa_autotune": (c.c_int, [P(_CSettings), P(c.c_double), c.c_int64, c.c_int32,
+                                   P(c.c_int32), P(c.c_float)]),
+        "rqa_autotune_clear": (None, []),
+        "rqa_autotune_last_error": (c.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -470,6 +474,32 @@ def cross_recurrence_plot(settings: Settings, x, y, i0: int = 0, j0: int = 0,
         return out
     bits = np.unpackbits(out.view(np.uint8), axis=1, bitorder="little")
     return bits[:, :cols]
+
+
+def autotune(settings: Settings, n_points: Optional[int] = None, series=None,
+             cross: bool = False) -> dict:
+    """Time every CTA-strip width on `series` (or on a built-in AR(1) series
+    of n_points values) and record the fastest for the settings' class; later
+    runs of the class use it.  Returns {"warps": best, "ms": {width: ms}}."""
+    P = ctypes.POINTER(ctypes.c_double)
+    if series is not None:
+        s = _f64(series)
+        ptr, n_points = s.ctypes.data_as(P), len(s)
+    else:
+        ptr = None
+    cs = _cs(settings)
+    best = ctypes.c_int32()
+    ms = (ctypes.c_float * 4)()
+    rc = load().rqa_autotune(ctypes.byref(cs), ptr, int(n_points), 1 if cross else 0,
+                             ctypes.byref(best), ms)
+    if rc:
+        raise RQAError(rc, "rqa_autotune", load().rqa_autotune_last_error().decode())
+    return {"warps": best.value, "ms": {w: ms[q] for q, w in enumerate((1, 2, 4, 8))}}
+
+
+def autotune_clear() -> None:
+    """Forget every width the autotuner recorded."""
+    load().rqa_autotune_clear()
 
 
 def pack_matrix(matrix) -> np.ndarray:
