@@ -138,6 +138,8 @@ typedef struct {
   int32_t launches;       /* kernels launched by the run                      */
   int32_t mode;           /* 0 RQA, 1 cross recurrence, 2 precomputed matrix  */
   int64_t n_cols;         /* columns: n_vec for RQA, n2 for cross recurrence  */
+  int64_t band_rows;      /* RQA: rows per band when strips were split into
+                             row bands to fill the GPU (0: not split)         */
 } rqa_stats_t;
 
 typedef struct rqa_handle rqa_handle;

@@ -212,10 +212,13 @@ __global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd) {
 }
 
 // ------------------------------------------------------- merge: diagonals
-// Diagonal k >= 1 (cells (i, i+k)) starts at column n-1 and ends at (0, k):
-// it crosses strips Q = 0 .. (n-1-k)/sw.  Each strip left the black run
-// touching its entry (a), the black run touching its exit (z), or an
-// all-black flag.
+// Diagonal k >= 1 (cells (i, i+k)) starts at (n-1-k, n-1) and ends at (0, k).
+// Walked in that order it crosses the items (strip Q, band g) one after the
+// other: it leaves an item through its left edge (column J0) or its top edge
+// (row R0), at row max(R0, J0 - k), and continues at the next cell up-left.
+// Each item left the black run touching the diagonal's entry (a), the black
+// run touching its exit (z), or an all-black flag.  With one band the items
+// are the strips, Q = 0 .. (n-1-k)/sw.
 __global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || S.cross) return;
@@ -223,22 +226,115 @@ __global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd) {
   BlockHist h{sh};
   h.init();
   const int64_t n = S.n, sw = S.sw;
+  const bool banded = S.nbands > 1;
+  const int64_t H = banded ? S.band_h : n;
   for (int64_t k = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t qlast = (n - 1 - k) / sw;
+    int64_t i = n - 1 - k;  // entry row of the current item
     uint64_t L = 0;
-    for (int64_t Q = 0; Q <= qlast; ++Q) {
-      const int64_t off = strip_offset(n, sw, Q) + k - 1;
-      const uint32_t z = S.dia_z[off];
+    for (;;) {
+      const int64_t Q = (n - 1 - (i + k)) / sw;
+      const int64_t J1 = n - Q * sw, J0 = J1 - sw;
+      const int64_t g = banded ? i / H : 0;
+      const int64_t R0 = g * H, R1 = R0 + H < n ? R0 + H : n;
+      const int64_t off = banded ? S.dia_off[Q * S.nbands + g] : strip_offset(n, sw, Q);
+      const int64_t o = off + k - band_klo(J1, sw, R1);
+      const uint32_t z = S.dia_z[o];
       if (z & 0x8000u) {
         L += (z & 0x7FFFu);
       } else {
-        const uint64_t first = L + S.dia_a[off];
+        const uint64_t first = L + S.dia_a[o];
         if (first) h.add(S, HIST_DIAG, first);
         L = z & 0x7FFFu;
       }
+      const int64_t ie = R0 > J0 - k ? R0 : J0 - k;  // the diagonal's top cell in the item
+      if (ie <= 0) break;
+      i = ie - 1;
     }
     if (L) h.add(S, HIST_DIAG, L);
+  }
+  h.flush(S);
+}
+
+// ------------------------------------------------------ merge: columns
+// Row bands only.  Column j (rows 0 .. j-1 of the upper triangle) crosses
+// bands gb = (j-1)/H down to 0.  Every band holds the column's first run in
+// col_a -- in band gb the run touching row j-1, above it the run touching
+// the band's bottom edge -- unless the column's segment there is one run, and
+// its top run in col_z (with a flag when the segment is one run); band 0
+// closed its top run itself unless it is one run or touches row j-1.  Join
+// them bottom-up; the final run touching row j-1 goes to colend for the
+// line-of-identity join.
+__global__ void merge_cols_kernel(SeriesDesc* __restrict__ sd) {
+  const SeriesDesc& S = sd[blockIdx.y];
+  if (S.n <= 0 || !S.hist || S.cross || S.nbands <= 1) return;
+  __shared__ uint32_t sh[3 * HB];
+  BlockHist h{sh};
+  h.init();
+  const int64_t n = S.n, H = S.band_h;
+  constexpr uint32_t LEN = 0x3FFFFFFFu, WHOLE = 1u << 30;
+  for (int64_t j = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gb = (j - 1) / H;
+    if (gb == 0) {  // one band: its first (or only) run is final
+      S.colend[j] = S.col_a[j];
+      continue;
+    }
+    const uint32_t zb = S.col_z[gb * n + j];
+    bool loi_open;
+    uint64_t loi_len, olen = 0;
+    uint32_t loi_col, ocol = 0;
+    if (zb & WHOLE) {
+      loi_open = true;
+      loi_len = zb & LEN;
+      loi_col = zb >> 31;
+    } else {
+      loi_open = false;
+      const uint32_t ce = S.col_a[gb * n + j];
+      loi_len = ce & 0x7FFFFFFFu;
+      loi_col = ce >> 31;
+      ocol = zb >> 31;
+      olen = zb & LEN;
+    }
+    for (int64_t g = gb - 1; g >= 0; --g) {
+      const uint32_t z = S.col_z[g * n + j];
+      if (z & WHOLE) {
+        const uint32_t zc = z >> 31;
+        const uint64_t zl = z & LEN;
+        if (loi_open) {
+          if (loi_col == zc) {
+            loi_len += zl;
+          } else {
+            loi_open = false;
+            ocol = zc;
+            olen = zl;
+          }
+        } else if (olen && ocol == zc) {
+          olen += zl;
+        } else {
+          emit2(h, S, ocol, olen);
+          ocol = zc;
+          olen = zl;
+        }
+      } else {
+        const uint32_t a = S.col_a[g * n + j];
+        const uint32_t ac = a >> 31;
+        const uint64_t al = a & 0x7FFFFFFFu;
+        if (loi_open) {
+          if (loi_col == ac) loi_len += al; else emit2(h, S, ac, al);
+          loi_open = false;
+        } else if (olen && ocol == ac) {
+          emit2(h, S, ocol, olen + al);
+        } else {
+          emit2(h, S, ocol, olen);
+          emit2(h, S, ac, al);
+        }
+        ocol = z >> 31;
+        olen = g > 0 ? (z & LEN) : 0;  // band 0 closed its own top run
+      }
+    }
+    emit2(h, S, ocol, olen);  // the open run touching row 0
+    S.colend[j] = (uint32_t)loi_len | (loi_col << 31);
   }
   h.flush(S);
 }
@@ -419,8 +515,8 @@ void launch_embed(SeriesDesc* d_sd, int count, int64_t max_n_mp, int sms, cudaSt
   if (blocks < 1) blocks = 1;
   embed_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
 }
-int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cross, int sms,
-                  cudaStream_t st) {
+int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cross, bool bands,
+                  int sms, cudaStream_t st) {
   int64_t blocks = (max_n + 255) / 256;
   if (blocks > 4 * sms) blocks = 4 * sms;
   if (blocks < 1) blocks = 1;
@@ -428,9 +524,14 @@ int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cro
   if (sym) {
     merge_rows_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
     merge_diags_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+    launched += 2;
+    if (bands) {
+      merge_cols_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+      ++launched;
+    }
     join_loi_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
     diag_full_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
-    launched += 4;
+    launched += 2;
   }
   if (cross) {
     merge_cross_diags_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);

@@ -81,19 +81,54 @@ int64_t cross_cell_count(int64_t n1, int64_t n2, int64_t w) {
 }
 
 struct Sizes {
-  int64_t n = 0, n2 = 0, hl = 0, nstrips = 0, ndesc = 0, wpr = 0;
+  int64_t n = 0, n2 = 0, hl = 0, nstrips = 0, ndesc = 0, nrowdesc = 0, wpr = 0;
+  int64_t nitems = 0;          // work items: strips, or (strip, band) pairs
+  int64_t band_h = 0, nbands = 1;
   int mp = 0;
   TileConfig tc{1, 4};
   bool f64 = false, cross = false, matrix = false;
   size_t hist = 0, ends = 0, cnt = 0, desc = 0, series = 0, series2 = 0, xe = 0, xe2 = 0;
+  size_t tab = 0, cols = 0;    // banded: item offset table, column descriptors
 };
+
+// Row-band height for an RQA series: RQA_BAND_ROWS if set (rounded up to a
+// multiple of 32; for tests and tuning), else bands only when the strips
+// alone give fewer than 7,104 warps (two per resident warp slot of the 80-
+// register kernel on 148 SMs) -- about 2,048 items of at least 1,024 rows.
+int64_t band_rows_for(int64_t n, int64_t sw, int64_t nstrips, int warps) {
+  if (const char* e = std::getenv("RQA_BAND_ROWS")) {
+    const int64_t h = std::atoll(e);
+    return h > 0 ? (h + 31) / 32 * 32 : 0;
+  }
+  if (n < 8192 || nstrips * warps >= 7104) return 0;
+  const int64_t rows = strip_offset(n, sw, nstrips);  // rows summed over strips
+  const int64_t h = (rows + 2047) / 2048;
+  return std::max<int64_t>(1024, (h + 31) / 32 * 32);
+}
+
+// Visit the items (Q, g) of a banded RQA series with their row range and the
+// range of diagonals k that can cross them.
+template <class F>
+void for_each_band_item(const Sizes& z, F&& f) {
+  const int64_t sw = 32LL * z.tc.warps * z.tc.cols;
+  for (int64_t Q = 0; Q < z.nstrips; ++Q) {
+    const int64_t J1 = z.n - Q * sw;
+    for (int64_t g = 0; g < z.nbands; ++g) {
+      const int64_t R0 = g * z.band_h;
+      if (R0 > J1 - 2) break;  // no row of the upper triangle in this band
+      const int64_t R1 = std::min(R0 + z.band_h, z.n);
+      const int64_t klo = band_klo(J1, sw, R1), khi = J1 - 1 - R0;
+      f(Q, g, std::min(R1, J1 - 1) - R0, khi - klo + 1);
+    }
+  }
+}
 
 // Device buffers of one series (RQA), one pair of series (cross
 // recurrence: rows from the N values, columns from the N2 values) or one
 // precomputed N x N2 bit matrix (its copy counted in `series`).
 Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross = false,
                 int64_t N2 = 0, bool copy_series2 = false, bool matrix = false,
-                int warps = 0) {
+                int warps = 0, bool allow_bands = false) {
   Sizes z;
   z.matrix = matrix;
   z.n = matrix ? N : nvec_of(st, N);
@@ -111,12 +146,27 @@ Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross 
   } else {
     z.nstrips = num_strips(z.n, sw);
     z.ndesc = strip_offset(z.n, sw, z.nstrips);
+    z.nrowdesc = z.ndesc;  // rows: strip-triangular, banded or not
+    const int64_t h = allow_bands ? band_rows_for(z.n, sw, z.nstrips, z.tc.warps) : 0;
+    if (h > 0 && h < z.n) {
+      z.band_h = h;
+      z.nbands = (z.n + h - 1) / h;
+      z.ndesc = 0;
+      for_each_band_item(z, [&](int64_t, int64_t, int64_t, int64_t cnt) {
+        z.ndesc += cnt;
+        ++z.nitems;
+      });
+      z.tab = align256(sizeof(int64_t) * static_cast<size_t>(z.nstrips * z.nbands));
+      z.cols = 2 * align256(sizeof(uint32_t) * static_cast<size_t>(z.nbands * z.n));
+    }
   }
+  if (z.nitems == 0) z.nitems = z.nstrips;
   z.hist = align256(sizeof(uint64_t) * 3 * static_cast<size_t>(z.hl + 1));
   z.ends = z.cross ? 0 : align256(sizeof(uint32_t) * 2 * static_cast<size_t>(z.n));
   z.cnt = align256(sizeof(uint64_t) * CNT_WORDS);
   // RQA: row_a, row_z, dia_a, dia_z; cross recurrence and matrices: dia_a, dia_z
-  z.desc = (z.cross ? 2 : 4) * align256(sizeof(uint16_t) * static_cast<size_t>(z.ndesc));
+  z.desc = 2 * align256(sizeof(uint16_t) * static_cast<size_t>(z.ndesc)) +
+           2 * align256(sizeof(uint16_t) * static_cast<size_t>(z.nrowdesc));
   if (matrix) {
     z.wpr = (z.n2 + 31) / 32;
     z.series = copy_series ? align256(sizeof(uint32_t) * static_cast<size_t>(z.n * z.wpr)) : 0;
@@ -194,10 +244,16 @@ TileConfig choose_tile(int64_t n, int m, int norm, bool f64, int kind) {
 
 size_t series_device_bytes(const rqa_settings& st, int64_t N) {
   // the narrowest strips (one warp) need the most descriptors: a run that
-  // batches this series with others, or an autotuned width, never needs more
-  const Sizes z = sizes_for(st, N, true, false, 0, false, false, 1);
-  return z.hist + z.ends + z.cnt + z.desc + z.series + z.xe + align256(sizeof(SeriesDesc)) +
-         align256(sizeof(Item) * static_cast<size_t>(z.nstrips)) + 256;
+  // batches this series with others, or an autotuned width, never needs more;
+  // row bands add item tables and column descriptors
+  size_t worst = 0;
+  for (const bool bands : {false, true}) {
+    const Sizes z = sizes_for(st, N, true, false, 0, false, false, 1, bands);
+    worst = std::max(worst, z.hist + z.ends + z.cnt + z.desc + z.series + z.xe + z.tab +
+                                z.cols + align256(sizeof(SeriesDesc)) +
+                                align256(sizeof(Item) * static_cast<size_t>(z.nitems)) + 256);
+  }
+  return worst;
 }
 
 Engine::Engine(int device) : dev_(device) {
@@ -309,7 +365,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     Sizes z;
     int cls = -1;
     bool run = false;
-    size_t o_hist, o_ends, o_cnt, o_desc, o_series, o_series2, o_xe, o_xe2;
+    size_t o_hist, o_ends, o_cnt, o_desc, o_series, o_series2, o_xe, o_xe2, o_tab, o_cols;
   };
   std::vector<P> plan(count);
   std::vector<int> dev_idx(count, -1);  // device slot of each runnable series
@@ -318,7 +374,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   std::map<Key, int> cls_of;
   std::vector<Key> classes;
   int64_t max_n = 0, max_n_mp = 0, total_items = 0;
-  bool any_fp32 = false, any_sym = false, any_cross = false;
+  bool any_fp32 = false, any_sym = false, any_cross = false, any_bands = false;
   for (int q = 0; q < count; ++q) {
     std::string msg;
     int s = validate_settings(&in[q].st, &msg);
@@ -408,15 +464,17 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     if (in[q].matrix)
       p.z = sizes_for(in[q].st, in[q].N, in[q].bits_dev == nullptr, true, in[q].N2, false, true,
                       warps);
-    else
+    else  // row bands for a single series, or a large one among others
       p.z = sizes_for(in[q].st, in[q].N, in[q].dev == nullptr, in[q].cross, in[q].N2,
-                      in[q].dev2 == nullptr, false, warps);
+                      in[q].dev2 == nullptr, false, warps,
+                      !in[q].cross && (count == 1 || nvec_of(in[q].st, in[q].N) >= 65536));
     dev_idx[q] = nrun++;
     (p.z.cross ? any_cross : any_sym) = true;
-    // kernel class: (m, norm, f64, warps, kind), kind 0 RQA, 1 cross, 2 matrix
+    // kernel class: (m, norm, f64, warps, kind), kind 0 RQA, 1 cross, 2 matrix,
+    // 3 RQA in row bands
     const Key k = p.z.matrix ? Key{0, 0, 0, p.z.tc.warps, 2}
                              : Key{in[q].st.m, in[q].st.norm, p.z.f64 ? 1 : 0, p.z.tc.warps,
-                                   p.z.cross ? 1 : 0};
+                                   p.z.cross ? 1 : p.z.nbands > 1 ? 3 : 0};
     auto it = cls_of.find(k);
     if (it == cls_of.end()) {
       it = cls_of.emplace(k, static_cast<int>(classes.size())).first;
@@ -428,7 +486,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       any_fp32 = true;
       max_n_mp = std::max(max_n_mp, (p.z.n + (p.z.cross ? p.z.n2 : 0)) * p.z.mp);
     }
-    total_items += p.z.nstrips;
+    total_items += p.z.nitems;
+    any_bands = any_bands || p.z.nbands > 1;
   }
   const int ncls = static_cast<int>(classes.size());
   if (ncls == 0) {  // nothing runnable: report the first validation failure
@@ -444,6 +503,12 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   off += align256(sizeof(SeriesDesc) * nrun);
   const size_t o_items = off;
   off += align256(sizeof(Item) * static_cast<size_t>(std::max<int64_t>(total_items, 1)));
+  const size_t o_tab0 = off;  // item offset tables of banded series
+  for (auto& p : plan)
+    if (p.run) {
+      p.o_tab = off;
+      off += p.z.tab;
+    }
   const size_t o_zero = off;
   const size_t o_queue = off;
   off += align256(sizeof(int) * ncls);
@@ -467,6 +532,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       off += p.z.ends;
       p.o_desc = off;
       off += p.z.desc;
+      p.o_cols = off;
+      off += p.z.cols;
     }
   const size_t zero_bytes = off - o_zero;
   const size_t o_series0 = off;
@@ -487,12 +554,12 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     }
   const size_t arena_bytes = off;
 
-  // host staging: [descs][items][hist readback][counter readback][series]
+  // host staging: [descs][items][band tables] (the arena's first o_zero bytes,
+  // copied in one piece) [hist readback][counter readback][series]
   size_t hoff = 0;
   const size_t h_sd = hoff;
-  hoff += align256(sizeof(SeriesDesc) * nrun);
-  const size_t h_items = hoff;
-  hoff += align256(sizeof(Item) * static_cast<size_t>(std::max<int64_t>(total_items, 1)));
+  const size_t h_items = o_items - o_sd;
+  hoff += o_zero - o_sd;
   const size_t h_hist = hoff;
   hoff += hist_bytes;
   const size_t h_cnt = hoff;
@@ -564,18 +631,24 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     d.eps = s.eps;
     d.band_override = s.band_override;
     d.hist = reinterpret_cast<unsigned long long*>(arena_ + p.o_hist);
-    if (p.z.cross) {
-      const size_t dbytes = p.z.desc / 2;
+    if (p.z.nbands > 1) {  // row bands: item offset table and column descriptors
+      d.band_h = static_cast<int32_t>(p.z.band_h);
+      d.nbands = static_cast<int32_t>(p.z.nbands);
+      d.dia_off = reinterpret_cast<const int64_t*>(arena_ + p.o_tab);
+      d.col_a = reinterpret_cast<uint32_t*>(arena_ + p.o_cols);
+      d.col_z = d.col_a + (p.z.cols / 2) / sizeof(uint32_t);
+    }
+    {
+      const size_t dbytes = align256(sizeof(uint16_t) * static_cast<size_t>(p.z.ndesc));
+      const size_t rbytes = align256(sizeof(uint16_t) * static_cast<size_t>(p.z.nrowdesc));
       d.dia_a = reinterpret_cast<uint16_t*>(arena_ + p.o_desc);
       d.dia_z = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + dbytes);
-    } else {
-      const size_t dbytes = p.z.desc / 4;
-      d.row_a = reinterpret_cast<uint16_t*>(arena_ + p.o_desc);
-      d.row_z = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + dbytes);
-      d.dia_a = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + 2 * dbytes);
-      d.dia_z = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + 3 * dbytes);
-      d.colend = reinterpret_cast<uint32_t*>(arena_ + p.o_ends);
-      d.rowend = d.colend + p.z.n;
+      if (!p.z.cross) {
+        d.row_a = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + 2 * dbytes);
+        d.row_z = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + 2 * dbytes + rbytes);
+        d.colend = reinterpret_cast<uint32_t*>(arena_ + p.o_ends);
+        d.rowend = d.colend + p.z.n;
+      }
     }
     d.counters = reinterpret_cast<unsigned long long*>(arena_ + p.o_cnt);
   }
@@ -591,9 +664,21 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       const P& p = plan[q];
       if (!p.run) continue;
       const int64_t sw = 32LL * p.z.tc.warps * p.z.tc.cols;
-      for (int64_t Q = 0; Q < p.z.nstrips; ++Q)  // strip height: the rows it spans
-        per[p.cls].push_back({p.z.cross ? p.z.n : p.z.n - Q * sw,
-                              Item{dev_idx[q], static_cast<int32_t>(Q)}});
+      if (p.z.nbands > 1) {  // items (Q, g), the table of their descriptor offsets
+        int64_t* tab = reinterpret_cast<int64_t*>(host_ + h_sd + (p.o_tab - o_sd));
+        std::fill(tab, tab + p.z.nstrips * p.z.nbands, int64_t(-1));
+        int64_t dpos = 0;
+        for_each_band_item(p.z, [&](int64_t Q, int64_t g, int64_t rows, int64_t cnt) {
+          tab[Q * p.z.nbands + g] = dpos;
+          dpos += cnt;
+          per[p.cls].push_back({rows, Item{dev_idx[q], static_cast<int32_t>(Q),
+                                           static_cast<int32_t>(g)}});
+        });
+      } else {
+        for (int64_t Q = 0; Q < p.z.nstrips; ++Q)  // strip height: the rows it spans
+          per[p.cls].push_back({p.z.cross ? p.z.n : p.z.n - Q * sw,
+                                Item{dev_idx[q], static_cast<int32_t>(Q), 0}});
+      }
     }
     int64_t pos = 0;
     for (int c = 0; c < ncls; ++c) {
@@ -628,6 +713,10 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       key.push_back(in[q].cross ? 1 : 0);
       key.push_back(in[q].matrix ? 1 : 0);
       key.push_back(reinterpret_cast<int64_t>(in[q].bits_dev));
+      // the plan's choices (strip width, row bands) may change between calls
+      // with the same shapes (autotuning, environment overrides)
+      key.push_back(plan[q].run ? plan[q].z.tc.warps : 0);
+      key.push_back(plan[q].run ? plan[q].z.band_h : 0);
       key.push_back(in[q].N2);
       key.push_back(reinterpret_cast<int64_t>(in[q].dev2));
     }
@@ -699,7 +788,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       const bool f64 = std::get<2>(classes[c]) != 0;
       const int warps = std::get<3>(classes[c]);
       const int kind = std::get<4>(classes[c]);
-      TileFn fn = kind == 2 ? tile_kernel_matrix(4) : tile_kernel_for(m, norm, 4, f64, kind == 1);
+      TileFn fn = kind == 2 ? tile_kernel_matrix(4)
+                            : tile_kernel_for(m, norm, 4, f64, kind == 1, kind == 3);
       if (!fn) return fail(RQA_EINVAL, "no tile kernel for this (m, norm)");
       const size_t smem = tile_smem_for(kind == 2 ? 1 : m, norm, f64, warps, 4);
       if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
@@ -732,7 +822,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     }
     if ((e = cudaEventRecordWithFlags(ev_[2], st, evflags)) != cudaSuccess)
       return cuda_fail(e, "cudaEventRecord");
-    launches += launch_merges(d_sd, nrun, max_n, any_sym, any_cross, sms_, st);
+    launches += launch_merges(d_sd, nrun, max_n, any_sym, any_cross, any_bands, sms_, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "merge kernels launch");
     if ((e = cudaMemcpyAsync(host_ + h_hist, arena_ + o_hist0, hist_bytes + cnt_bytes,
                              cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -817,6 +907,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     s.band_bound = p.z.f64 ? 0.0 : d.bound_rel;
     s.exact = (p.z.f64 || p.z.matrix || d.band_rel >= d.bound_rel) ? 1 : 0;
     s.strip_width = 32 * p.z.tc.warps * p.z.tc.cols;
+    s.band_rows = p.z.nbands > 1 ? p.z.band_h : 0;
     s.warps_per_cta = p.z.tc.warps;
     s.cols_per_lane = p.z.tc.cols;
     s.kernel_ms = tile_ms_;

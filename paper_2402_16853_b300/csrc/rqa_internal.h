@@ -28,6 +28,14 @@ struct SeriesDesc {
   // word w of a row is column 32 w + b; s, s2, xe, xe2 are unused
   const uint32_t* bits;
   int64_t wpr;          // words per row, ceil(n2 / 32)
+  // ---- row bands (RQA only): with nbands > 1, CTA strip Q is split into
+  // items (Q, g) of rows [g H, (g+1) H) so that series too small to fill the
+  // GPU with strips alone still do; 0 / 1: one band of all rows
+  int32_t band_h;       // H, a multiple of 32
+  int32_t nbands;       // ceil(n / H)
+  const int64_t* dia_off;  // [nstrips][nbands] diagonal-descriptor offset of item (Q, g)
+  uint32_t* col_a;      // [nbands][n] first run of column j in band g (touches its bottom)
+  uint32_t* col_z;      // [nbands][n] run of column j touching band g's top edge
   // ---- filled by the prepare kernel
   double center, scale; // x32 = fl32((s - center) * scale)
   float thr;            // FP32 threshold: eps*scale (L1, max) or its square (L2)
@@ -81,7 +89,15 @@ __host__ __device__ inline int64_t cross_num_strips(int64_t n2, int64_t sw) {
 struct Item {
   int32_t series;
   int32_t strip;
+  int32_t band;
 };
+
+// Diagonals k >= 1 that can cross item (Q, g) of an RQA strip [J1 - sw, J1)
+// and band rows [R0, R1): k from band_klo to J1 - 1 - R0.
+__host__ __device__ inline int64_t band_klo(int64_t J1, int64_t sw, int64_t R1) {
+  const int64_t k = J1 - sw - R1 + 1;
+  return k > 1 ? k : 1;
+}
 
 struct TileConfig {
   int warps;   // warps per CTA (warps of one CTA strip, right to left)

@@ -12,13 +12,13 @@ using TileFn = void (*)(const SeriesDesc*, const Item*, int, int*);
 
 // Fused tile kernel for embedding dimension m (1..10), norm (0 max, 1 L2,
 // 2 L1), columns per lane `cols` (4), FP64-everywhere or FP32 + recheck, and
-// the symmetric (RQA) or cross-recurrence matrix.
-TileFn tile_kernel_for(int m, int norm, int cols, bool f64, bool cross);
+// the symmetric (RQA, with or without row bands) or cross-recurrence matrix.
+TileFn tile_kernel_for(int m, int norm, int cols, bool f64, bool cross, bool bands = false);
 size_t tile_smem_for(int m, int norm, bool f64, int warps, int cols);
 
-TileFn tile_kernel_norm0(int m, int cols, bool f64);
-TileFn tile_kernel_norm1(int m, int cols, bool f64);
-TileFn tile_kernel_norm2(int m, int cols, bool f64);
+TileFn tile_kernel_norm0(int m, int cols, bool f64, bool bands);
+TileFn tile_kernel_norm1(int m, int cols, bool f64, bool bands);
+TileFn tile_kernel_norm2(int m, int cols, bool f64, bool bands);
 TileFn tile_kernel_cross_norm0(int m, int cols, bool f64);
 TileFn tile_kernel_cross_norm1(int m, int cols, bool f64);
 TileFn tile_kernel_cross_norm2(int m, int cols, bool f64);
@@ -29,10 +29,11 @@ void launch_prepare(SeriesDesc* d_sd, int count, cudaStream_t st);
 void launch_embed(SeriesDesc* d_sd, int count, int64_t max_n_mp, int sms, cudaStream_t st);
 // The merge and finalize kernels; `sym` / `cross` say whether the set holds
 // RQA series (rows, diagonals, line-of-identity join) and cross-recurrence
-// series (diagonals of the rectangle); max_n bounds the rows, columns and
-// diagonals of any series.  Returns the number of kernels launched.
-int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cross, int sms,
-                  cudaStream_t st);
+// series (diagonals of the rectangle), `bands` whether an RQA series runs in
+// row bands (column joins); max_n bounds the rows, columns and diagonals of
+// any series.  Returns the number of kernels launched.
+int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cross, bool bands,
+                  int sms, cudaStream_t st);
 void launch_plot(const SeriesDesc* d_sd, int64_t i0, int64_t j0, int64_t rows, int64_t cols,
                  uint32_t* out, int f64, int sms, cudaStream_t st);
 void launch_sample(const SeriesDesc* d_sd, const int64_t* ii, const int64_t* jj, int64_t count,

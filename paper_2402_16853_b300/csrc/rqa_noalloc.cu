@@ -219,7 +219,7 @@ extern "C" int rqa_run_noalloc(const rqa_settings* settings, const double* dev_s
                               dim3(32 * tc.warps), args, smem, st)) != cudaSuccess)
       return fail(RQA_ECUDA, std::string("tile kernel launch: ") + cudaGetErrorString(e));
   }
-  launch_merges(d_sd, 1, n, true, false, sms, st);
+  launch_merges(d_sd, 1, n, true, false, false, sms, st);
   if ((e = cudaGetLastError()) != cudaSuccess)
     return fail(RQA_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   unsigned long long status = 0;

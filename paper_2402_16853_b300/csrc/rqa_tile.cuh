@@ -451,7 +451,7 @@ inline size_t tile_smem_bytes(int warps, int row_elems, int elem_bytes, int cols
 }
 
 // ------------------------------------------------------------------ kernel
-template <int M, int NORM, int C, bool F64, bool XR, bool MX = false>
+template <int M, int NORM, int C, bool F64, bool XR, bool MX = false, bool BD = false>
 __global__ void __launch_bounds__(256, 3)
 tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, int nitems,
             int* __restrict__ queue) {
@@ -517,14 +517,24 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
     uint16_t* __restrict__ dia_a = Sp->dia_a;
     uint16_t* __restrict__ dia_z = Sp->dia_z;
     const int J1 = ncol - wi.strip * SW;              // strip: [J1-SW, J1)
+    // RQA row band g: rows [R0, R1) of the strip (one band: all rows); the
+    // banded code is a separate instantiation so the unbanded one stays lean
+    constexpr bool banded = BD && !XR;
+    const int g = banded ? wi.band : 0;
+    const int R0 = banded ? g * Sp->band_h : 0;
+    const int R1 = banded ? min(R0 + Sp->band_h, n) : n;
     // descriptors of diagonal k sit at off + k - klo (RQA: k >= 1 in a
-    // strip-triangular layout; cross: the n + SW - 1 diagonals of the strip)
-    const int64_t off = XR ? (int64_t)wi.strip * cross_strip_diags(n, SW)
-                           : strip_offset(n, SW, wi.strip);
-    const int klo = XR ? J1 - SW - (n - 1) : 1;
+    // strip-triangular layout, or per item when banded; cross: the n + SW - 1
+    // diagonals of the strip)
+    const int64_t off = XR       ? (int64_t)wi.strip * cross_strip_diags(n, SW)
+                        : banded ? Sp->dia_off[(int64_t)wi.strip * Sp->nbands + g]
+                                 : strip_offset(n, SW, wi.strip);
+    const int klo = XR ? J1 - SW - (n - 1) : banded ? (int)band_klo(J1, SW, R1) : 1;
+    // row descriptors keep the strip-triangular layout (rows never cross bands)
+    const int64_t roff = banded ? strip_offset(n, SW, wi.strip) : off;
     const int jw1 = J1 - warp * 32 * C;              // warp: [jw0, jw1)
     const int jw0 = jw1 - 32 * C;
-    const int wl_geo = XR ? (J1 - 1) / (32 * C) : (J1 - 2) / (32 * C);
+    const int wl_geo = XR ? (J1 - 1) / (32 * C) : (J1 - 2 - R0) / (32 * C);
     const int wlast = wl_geo < NW - 1 ? wl_geo : NW - 1;
     const int nh = XR ? (int)Sp->hl : n;             // longest possible line
     const HistSink hs{sh_hist, Sp->hist, (uint32_t)nh, &Sp->counters[CNT_STATUS]};
@@ -532,9 +542,20 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
     if (warp <= wlast) {
       const bool leftmost = warp == wlast;
       const int jmax = jw1 - 1;
-      // RQA: rows above the line of identity; cross: all n rows
-      const int bhi = XR ? (n - 1) >> 5 : (jmax - 1) >> 5;
-      const int bhi_left = leftmost ? -1 : XR ? bhi : ((jmax - 32 * C - 1) >> 5);
+      // RQA: rows above the line of identity (within the band); cross: all n rows
+      const int bhi = XR       ? (n - 1) >> 5
+                      : banded ? min((jmax - 1) >> 5, (R1 - 1) >> 5)
+                               : (jmax - 1) >> 5;
+      const int bhi_left = leftmost ? -1
+                           : XR     ? bhi
+                           : banded ? min((jmax - 32 * C - 1) >> 5, (R1 - 1) >> 5)
+                                    : (jmax - 32 * C - 1) >> 5;
+      const int blo = R0 >> 5;
+      // the band cuts this warp's triangle: diagonals continue below its bottom
+      const bool cut_below = banded && ((jmax - 1) >> 5) > ((R1 - 1) >> 5);
+      // first run of each column: next to the line of identity (colend), or
+      // per band, touching the band's bottom edge or the line of identity
+      uint32_t* __restrict__ colfirst = banded ? Sp->col_a + (int64_t)g * n : colend;
       uint32_t* ring_in = warp > 0 ? ring + (warp - 1) * RING * 64 : nullptr;
       uint32_t* ring_out = !leftmost ? ring + warp * RING * 64 : nullptr;
       int seq_in = 0, seq_out = 0;
@@ -563,7 +584,9 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           }
         }
         cst_s[c * 32 + lane] = ST_FLAG;
-        dU_s[c * 32 + lane] = 0;
+        // carry from below the first block: a run touching the band's bottom
+        // edge where the diagonal continues there (cell (R1, j) with j > R1)
+        dU_s[c * 32 + lane] = (cut_below && j > R1) ? DG_EDGE : 0u;
       }
       int bufo = 0;  // which half of dU_s holds the carries of the block below
       ShortCounts sc{0, 0, 0, 0, 0};
@@ -572,7 +595,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
       const float band = Sp->band;
       bool ok = true;
 
-      for (int b = bhi; b >= 0 && ok; --b) {
+      for (int b = bhi; b >= blo && ok; --b) {
         const int r0 = b << 5;
         if constexpr (!MX) {  // row vectors of rows r0 .. r0+31 into this warp's buffer
           const int i = r0 + lane;
@@ -773,7 +796,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
               if constexpr (XR) {
                 if (len) hs.add2(col, len);
               } else {
-                colend[j] = len | (col << 31);
+                colfirst[j] = len | (col << 31);
               }
             };
             if (vt == 32)
@@ -789,7 +812,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             if (lo <= 31 && !(rst & ST_DONE) && row_valid) {
               auto emitr = [&](uint32_t col, uint32_t len) { hs.add2(col, len); };
               auto firstr = [&](uint32_t col, uint32_t len) {
-                row_a[off + irow] = (uint16_t)((len << 1) | col);
+                row_a[roff + irow] = (uint16_t)((len << 1) | col);
               };
               if (lo <= 0)
                 rst = scan2_full(RW, rst, sc, emitr, firstr);
@@ -798,8 +821,8 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
               if (lo >= 0) {  // the row ends here, at column irow + 1
                 const uint32_t len = rst & ST_LEN, col = (rst >> 28) & 1u;
                 const uint32_t same = (rst >> 29) & 1u;
-                row_z[off + irow] = (uint16_t)((len << 2) | (same << 1) | col);
-                if (same) row_a[off + irow] = 0;
+                row_z[roff + irow] = (uint16_t)((len << 2) | (same << 1) | col);
+                if (same) row_a[roff + irow] = 0;
                 rst = ST_DONE;
               }
             }
@@ -851,8 +874,8 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             const uint32_t len = rst & ST_LEN, col = (rst >> 28) & 1u;
             const uint32_t same = (rst >> 29) & 1u;
             if (len > 0) {
-              row_z[off + irow] = (uint16_t)((len << 2) | (same << 1) | col);
-              if (same) row_a[off + irow] = 0;
+              row_z[roff + irow] = (uint16_t)((len << 2) | (same << 1) | col);
+              if (same) row_a[roff + irow] = 0;
             }
           }
           const int kx = jw0 - r0 + lane - 32;  // diagonal leaving through the left edge
@@ -873,21 +896,28 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
       }
 
       if (ok) {
-        // ---- top border: close column runs, record diagonal ends (row 0)
+        // ---- top border (row R0): close or record column runs, record the
+        // ends of the diagonals leaving through it (k = j - R0 at (R0, j))
 #pragma unroll 1
         for (int c = 0; c < C; ++c) {
           const int j = jw0 + 32 * c + lane;
-          if (j >= (XR ? 0 : 1)) {
+          if (j >= (XR ? 0 : R0 + 1)) {
             const uint32_t st = cst_s[c * 32 + lane];
             const uint32_t len = st & ST_LEN, col = (st >> 28) & 1u;
-            if (len > 0) {
-              if (!XR && (st & ST_FLAG))
-                colend[j] = len | (col << 31);
-              else
-                hs.add2(col, len);
+            const bool whole = (st & ST_FLAG) != 0;  // one run over the column's segment
+            if (!banded || (R0 == 0 && (j <= R1 || !whole))) {
+              if (len > 0) {
+                if (!XR && whole)
+                  colfirst[j] = len | (col << 31);
+                else
+                  hs.add2(col, len);
+              }
+            } else {  // the run continues in the band above, or below: join later
+              Sp->col_z[(int64_t)g * n + j] = len | (whole ? (1u << 30) : 0u) | (col << 31);
             }
-            const uint32_t du = dU_s[bufo * C * 32 + c * 32 + lane];  // k = j ends at (0, j)
-            dia_z[off + j - klo] = (uint16_t)((du & ST_LEN) | ((du & DG_EDGE) ? 0x8000u : 0u));
+            const uint32_t du = dU_s[bufo * C * 32 + c * 32 + lane];
+            dia_z[off + (j - R0) - klo] =
+                (uint16_t)((du & ST_LEN) | ((du & DG_EDGE) ? 0x8000u : 0u));
           }
         }
       }

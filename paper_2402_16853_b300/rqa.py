@@ -79,7 +79,8 @@ class _CStats(ctypes.Structure):
                 ("ctas", ctypes.c_int32), ("kernel_ms", ctypes.c_float),
                 ("total_ms", ctypes.c_float), ("h2d_bytes", ctypes.c_int64),
                 ("d2h_bytes", ctypes.c_int64), ("launches", ctypes.c_int32),
-                ("mode", ctypes.c_int32), ("n_cols", ctypes.c_int64)]
+                ("mode", ctypes.c_int32), ("n_cols", ctypes.c_int64),
+                ("band_rows", ctypes.c_int64)]
 
 
 MEASURE_FIELDS = list(_MEAS_D + _MEAS_I)
