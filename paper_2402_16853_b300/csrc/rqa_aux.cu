@@ -341,11 +341,12 @@ __global__ void merge_cols_kernel(SeriesDesc* __restrict__ sd) {
 
 // ------------------------------------------------ merge: cross diagonals
 // Cross recurrence: diagonal k (cells (i, i+k), -(n1-1) <= k <= n2-1) runs
-// from its bottom-right end, column min(n2-1, n1-1+k), to its top-left end,
-// column max(0, k), through strips Qa .. Qz (strip Q covers columns
-// [n2 - (Q+1) sw, n2 - Q sw)).  The descriptors mean what they mean for
-// RQA; runs touching the matrix border were closed in the tile kernel or
-// are closed here at the diagonal's ends.
+// from its bottom-right end, (min(n1-1, n2-1-k), ...), to its top-left end
+// at row max(0, -k), through items (strip Q, band g): strip Q covers
+// columns [n2 - (Q+1) sw, n2 - Q sw), band g rows [g H, (g+1) H) (one band:
+// all rows); the diagonal leaves an item at row max(R0, J0 - k).  The
+// descriptors mean what they mean for RQA; runs touching the matrix border
+// were closed in the tile kernel or are closed here at the diagonal's ends.
 __global__ void merge_cross_diags_kernel(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || !S.cross) return;
@@ -353,16 +354,21 @@ __global__ void merge_cross_diags_kernel(SeriesDesc* __restrict__ sd) {
   BlockHist h{sh};
   h.init();
   const int64_t n1 = S.n, n2 = S.n2, sw = S.sw, nd = cross_strip_diags(n1, sw);
+  const bool banded = S.nbands > 1;
+  const int64_t H = banded ? S.band_h : n1;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n1 + n2 - 1;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = t - (n1 - 1);
-    const int64_t jlo = k > 0 ? k : 0;
-    const int64_t jhi = n1 - 1 + k < n2 - 1 ? n1 - 1 + k : n2 - 1;
-    const int64_t qa = (n2 - 1 - jhi) / sw, qz = (n2 - 1 - jlo) / sw;
+    int64_t i = n1 - 1 < n2 - 1 - k ? n1 - 1 : n2 - 1 - k;  // bottom-right end
+    const int64_t itop = k >= 0 ? 0 : -k;                   // top-left end
     uint64_t L = 0;
-    for (int64_t Q = qa; Q <= qz; ++Q) {
-      const int64_t klo = n2 - (Q + 1) * sw - (n1 - 1);
-      const int64_t o = Q * nd + (k - klo);
+    for (;;) {
+      const int64_t Q = (n2 - 1 - (i + k)) / sw;
+      const int64_t J1 = n2 - Q * sw, J0 = J1 - sw;
+      const int64_t g = banded ? i / H : 0;
+      const int64_t R0 = g * H, R1 = R0 + H < n1 ? R0 + H : n1;
+      const int64_t off = banded ? S.dia_off[Q * S.nbands + g] : Q * nd;
+      const int64_t o = off + (k - (J0 - (R1 - 1)));
       const uint32_t z = S.dia_z[o];
       if (z & 0x8000u) {
         L += (z & 0x7FFFu);
@@ -371,8 +377,59 @@ __global__ void merge_cross_diags_kernel(SeriesDesc* __restrict__ sd) {
         if (first) h.add(S, HIST_DIAG, first);
         L = z & 0x7FFFu;
       }
+      const int64_t ie = R0 > J0 - k ? R0 : J0 - k;
+      if (ie <= itop) break;
+      i = ie - 1;
     }
     if (L) h.add(S, HIST_DIAG, L);
+  }
+  h.flush(S);
+}
+
+// ------------------------------------------------ merge: cross columns
+// Cross recurrence in row bands: column j crosses bands nbands-1 .. 0.  The
+// last band closed its first run at the matrix border; every other band
+// holds its first run (col_a, touching its bottom edge) unless the column's
+// segment there is one run, and every band but 0 its top run (col_z, with a
+// whole-segment flag; band 0 records it only when whole).  Join bottom-up.
+__global__ void merge_cross_cols_kernel(SeriesDesc* __restrict__ sd) {
+  const SeriesDesc& S = sd[blockIdx.y];
+  if (S.n <= 0 || !S.hist || !S.cross || S.nbands <= 1) return;
+  __shared__ uint32_t sh[3 * HB];
+  BlockHist h{sh};
+  h.init();
+  const int64_t n2 = S.n2, nb = S.nbands;
+  constexpr uint32_t LEN = 0x3FFFFFFFu, WHOLE = 1u << 30;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n2;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t zl = S.col_z[(nb - 1) * n2 + j];
+    uint32_t ocol = zl >> 31;
+    uint64_t olen = zl & LEN;
+    for (int64_t g = nb - 2; g >= 0; --g) {
+      const uint32_t z = S.col_z[g * n2 + j];
+      if (z & WHOLE) {
+        if (olen && ocol == (z >> 31)) {
+          olen += z & LEN;
+        } else {
+          emit2(h, S, ocol, olen);
+          ocol = z >> 31;
+          olen = z & LEN;
+        }
+      } else {
+        const uint32_t a = S.col_a[g * n2 + j];
+        const uint32_t ac = a >> 31;
+        const uint64_t al = a & 0x7FFFFFFFu;
+        if (olen && ocol == ac) {
+          emit2(h, S, ocol, olen + al);
+        } else {
+          emit2(h, S, ocol, olen);
+          emit2(h, S, ac, al);
+        }
+        ocol = z >> 31;
+        olen = g > 0 ? (z & LEN) : 0;  // band 0 closed its own top run
+      }
+    }
+    emit2(h, S, ocol, olen);
   }
   h.flush(S);
 }
@@ -536,6 +593,10 @@ int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cro
   if (cross) {
     merge_cross_diags_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
     launched += 1;
+    if (bands) {
+      merge_cross_cols_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+      ++launched;
+    }
   }
   return launched;
 }

@@ -91,32 +91,37 @@ struct Sizes {
   size_t tab = 0, cols = 0;    // banded: item offset table, column descriptors
 };
 
-// Row-band height for an RQA series: RQA_BAND_ROWS if set (rounded up to a
-// multiple of 32; for tests and tuning), else bands only when the strips
-// alone give fewer than 7,104 warps (two per resident warp slot of the 80-
-// register kernel on 148 SMs) -- about 2,048 items of at least 1,024 rows.
-int64_t band_rows_for(int64_t n, int64_t sw, int64_t nstrips, int warps) {
+// Row-band height: RQA_BAND_ROWS if set (rounded up to a multiple of 32; for
+// tests and tuning), else bands only when the strips alone give fewer than
+// 7,104 warps (two per resident warp slot of the 80-register kernel on 148
+// SMs) -- about 2,048 items of at least 1,024 rows.  `rows` is the number of
+// rows summed over the strips.
+int64_t band_rows_for(int64_t n, int64_t rows, int64_t nstrips, int warps) {
   if (const char* e = std::getenv("RQA_BAND_ROWS")) {
     const int64_t h = std::atoll(e);
     return h > 0 ? (h + 31) / 32 * 32 : 0;
   }
   if (n < 8192 || nstrips * warps >= 7104) return 0;
-  const int64_t rows = strip_offset(n, sw, nstrips);  // rows summed over strips
   const int64_t h = (rows + 2047) / 2048;
   return std::max<int64_t>(1024, (h + 31) / 32 * 32);
 }
 
-// Visit the items (Q, g) of a banded RQA series with their row range and the
-// range of diagonals k that can cross them.
+// Visit the items (Q, g) of a banded series with the rows they hold and the
+// number of diagonals k that can cross them: RQA strips hold the rows above
+// the line of identity, cross-recurrence and matrix strips all n rows.
 template <class F>
 void for_each_band_item(const Sizes& z, F&& f) {
   const int64_t sw = 32LL * z.tc.warps * z.tc.cols;
   for (int64_t Q = 0; Q < z.nstrips; ++Q) {
-    const int64_t J1 = z.n - Q * sw;
+    const int64_t J1 = (z.cross ? z.n2 : z.n) - Q * sw;
     for (int64_t g = 0; g < z.nbands; ++g) {
       const int64_t R0 = g * z.band_h;
-      if (R0 > J1 - 2) break;  // no row of the upper triangle in this band
       const int64_t R1 = std::min(R0 + z.band_h, z.n);
+      if (z.cross) {
+        f(Q, g, R1 - R0, sw + (R1 - R0) - 1);
+        continue;
+      }
+      if (R0 > J1 - 2) break;  // no row of the upper triangle in this band
       const int64_t klo = band_klo(J1, sw, R1), khi = J1 - 1 - R0;
       f(Q, g, std::min(R1, J1 - 1) - R0, khi - klo + 1);
     }
@@ -147,7 +152,10 @@ Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross 
     z.nstrips = num_strips(z.n, sw);
     z.ndesc = strip_offset(z.n, sw, z.nstrips);
     z.nrowdesc = z.ndesc;  // rows: strip-triangular, banded or not
-    const int64_t h = allow_bands ? band_rows_for(z.n, sw, z.nstrips, z.tc.warps) : 0;
+  }
+  {
+    const int64_t rows = z.cross ? z.n * z.nstrips : z.nrowdesc;  // rows over all strips
+    const int64_t h = allow_bands ? band_rows_for(z.n, rows, z.nstrips, z.tc.warps) : 0;
     if (h > 0 && h < z.n) {
       z.band_h = h;
       z.nbands = (z.n + h - 1) / h;
@@ -157,7 +165,7 @@ Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross 
         ++z.nitems;
       });
       z.tab = align256(sizeof(int64_t) * static_cast<size_t>(z.nstrips * z.nbands));
-      z.cols = 2 * align256(sizeof(uint32_t) * static_cast<size_t>(z.nbands * z.n));
+      z.cols = 2 * align256(sizeof(uint32_t) * static_cast<size_t>(z.nbands * z.n2));
     }
   }
   if (z.nitems == 0) z.nitems = z.nstrips;
@@ -461,20 +469,22 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       warps = choose_tile(group_cols[g], std::get<1>(g), std::get<2>(g), std::get<3>(g) != 0,
                           std::get<0>(g)).warps;
     }
+    // row bands for a single series, or a large one among others
+    const bool bands_ok = count == 1 || cols_of(q) >= 65536;
     if (in[q].matrix)
       p.z = sizes_for(in[q].st, in[q].N, in[q].bits_dev == nullptr, true, in[q].N2, false, true,
-                      warps);
-    else  // row bands for a single series, or a large one among others
+                      warps, bands_ok);
+    else
       p.z = sizes_for(in[q].st, in[q].N, in[q].dev == nullptr, in[q].cross, in[q].N2,
-                      in[q].dev2 == nullptr, false, warps,
-                      !in[q].cross && (count == 1 || nvec_of(in[q].st, in[q].N) >= 65536));
+                      in[q].dev2 == nullptr, false, warps, bands_ok);
     dev_idx[q] = nrun++;
     (p.z.cross ? any_cross : any_sym) = true;
     // kernel class: (m, norm, f64, warps, kind), kind 0 RQA, 1 cross, 2 matrix,
-    // 3 RQA in row bands
-    const Key k = p.z.matrix ? Key{0, 0, 0, p.z.tc.warps, 2}
+    // plus 3 for the row-band instantiation of each
+    const int bk = p.z.nbands > 1 ? 3 : 0;
+    const Key k = p.z.matrix ? Key{0, 0, 0, p.z.tc.warps, 2 + bk}
                              : Key{in[q].st.m, in[q].st.norm, p.z.f64 ? 1 : 0, p.z.tc.warps,
-                                   p.z.cross ? 1 : p.z.nbands > 1 ? 3 : 0};
+                                   (p.z.cross ? 1 : 0) + bk};
     auto it = cls_of.find(k);
     if (it == cls_of.end()) {
       it = cls_of.emplace(k, static_cast<int>(classes.size())).first;
@@ -788,10 +798,11 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       const bool f64 = std::get<2>(classes[c]) != 0;
       const int warps = std::get<3>(classes[c]);
       const int kind = std::get<4>(classes[c]);
-      TileFn fn = kind == 2 ? tile_kernel_matrix(4)
-                            : tile_kernel_for(m, norm, 4, f64, kind == 1, kind == 3);
+      const bool banded = kind >= 3;
+      TileFn fn = kind % 3 == 2 ? tile_kernel_matrix(4, banded)
+                                : tile_kernel_for(m, norm, 4, f64, kind % 3 == 1, banded);
       if (!fn) return fail(RQA_EINVAL, "no tile kernel for this (m, norm)");
-      const size_t smem = tile_smem_for(kind == 2 ? 1 : m, norm, f64, warps, 4);
+      const size_t smem = tile_smem_for(kind % 3 == 2 ? 1 : m, norm, f64, warps, 4);
       if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem))) != cudaSuccess)

@@ -12,18 +12,18 @@ using TileFn = void (*)(const SeriesDesc*, const Item*, int, int*);
 
 // Fused tile kernel for embedding dimension m (1..10), norm (0 max, 1 L2,
 // 2 L1), columns per lane `cols` (4), FP64-everywhere or FP32 + recheck, and
-// the symmetric (RQA, with or without row bands) or cross-recurrence matrix.
+// the symmetric (RQA) or cross-recurrence matrix, with or without row bands.
 TileFn tile_kernel_for(int m, int norm, int cols, bool f64, bool cross, bool bands = false);
 size_t tile_smem_for(int m, int norm, bool f64, int warps, int cols);
 
 TileFn tile_kernel_norm0(int m, int cols, bool f64, bool bands);
 TileFn tile_kernel_norm1(int m, int cols, bool f64, bool bands);
 TileFn tile_kernel_norm2(int m, int cols, bool f64, bool bands);
-TileFn tile_kernel_cross_norm0(int m, int cols, bool f64);
-TileFn tile_kernel_cross_norm1(int m, int cols, bool f64);
-TileFn tile_kernel_cross_norm2(int m, int cols, bool f64);
+TileFn tile_kernel_cross_norm0(int m, int cols, bool f64, bool bands);
+TileFn tile_kernel_cross_norm1(int m, int cols, bool f64, bool bands);
+TileFn tile_kernel_cross_norm2(int m, int cols, bool f64, bool bands);
 // Line detection over a precomputed bit matrix (no distances).
-TileFn tile_kernel_matrix(int cols);
+TileFn tile_kernel_matrix(int cols, bool bands = false);
 
 void launch_prepare(SeriesDesc* d_sd, int count, cudaStream_t st);
 void launch_embed(SeriesDesc* d_sd, int count, int64_t max_n_mp, int sms, cudaStream_t st);

@@ -517,21 +517,21 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
     uint16_t* __restrict__ dia_a = Sp->dia_a;
     uint16_t* __restrict__ dia_z = Sp->dia_z;
     const int J1 = ncol - wi.strip * SW;              // strip: [J1-SW, J1)
-    // RQA row band g: rows [R0, R1) of the strip (one band: all rows); the
-    // banded code is a separate instantiation so the unbanded one stays lean
-    constexpr bool banded = BD && !XR;
+    // Row band g: rows [R0, R1) of the strip (one band: all rows); the banded
+    // code is a separate instantiation so the unbanded one stays lean
+    constexpr bool banded = BD;
     const int g = banded ? wi.band : 0;
     const int R0 = banded ? g * Sp->band_h : 0;
     const int R1 = banded ? min(R0 + Sp->band_h, n) : n;
     // descriptors of diagonal k sit at off + k - klo (RQA: k >= 1 in a
-    // strip-triangular layout, or per item when banded; cross: the n + SW - 1
-    // diagonals of the strip)
-    const int64_t off = XR       ? (int64_t)wi.strip * cross_strip_diags(n, SW)
-                        : banded ? Sp->dia_off[(int64_t)wi.strip * Sp->nbands + g]
-                                 : strip_offset(n, SW, wi.strip);
-    const int klo = XR ? J1 - SW - (n - 1) : banded ? (int)band_klo(J1, SW, R1) : 1;
+    // strip-triangular layout; cross: the n + SW - 1 diagonals of the strip;
+    // banded: per item, from the series' item table)
+    const int64_t off = banded ? Sp->dia_off[(int64_t)wi.strip * Sp->nbands + g]
+                        : XR   ? (int64_t)wi.strip * cross_strip_diags(n, SW)
+                               : strip_offset(n, SW, wi.strip);
+    const int klo = XR ? J1 - SW - (R1 - 1) : banded ? (int)band_klo(J1, SW, R1) : 1;
     // row descriptors keep the strip-triangular layout (rows never cross bands)
-    const int64_t roff = banded ? strip_offset(n, SW, wi.strip) : off;
+    const int64_t roff = (banded && !XR) ? strip_offset(n, SW, wi.strip) : off;
     const int jw1 = J1 - warp * 32 * C;              // warp: [jw0, jw1)
     const int jw0 = jw1 - 32 * C;
     const int wl_geo = XR ? (J1 - 1) / (32 * C) : (J1 - 2 - R0) / (32 * C);
@@ -543,7 +543,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
       const bool leftmost = warp == wlast;
       const int jmax = jw1 - 1;
       // RQA: rows above the line of identity (within the band); cross: all n rows
-      const int bhi = XR       ? (n - 1) >> 5
+      const int bhi = XR       ? (R1 - 1) >> 5
                       : banded ? min((jmax - 1) >> 5, (R1 - 1) >> 5)
                                : (jmax - 1) >> 5;
       const int bhi_left = leftmost ? -1
@@ -551,11 +551,15 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
                            : banded ? min((jmax - 32 * C - 1) >> 5, (R1 - 1) >> 5)
                                     : (jmax - 32 * C - 1) >> 5;
       const int blo = R0 >> 5;
-      // the band cuts this warp's triangle: diagonals continue below its bottom
-      const bool cut_below = banded && ((jmax - 1) >> 5) > ((R1 - 1) >> 5);
+      // the band cuts this warp's triangle (cross: the rectangle) so diagonals
+      // continue below its bottom
+      const bool cut_below =
+          banded && (XR ? R1 < n : ((jmax - 1) >> 5) > ((R1 - 1) >> 5));
       // first run of each column: next to the line of identity (colend), or
-      // per band, touching the band's bottom edge or the line of identity
-      uint32_t* __restrict__ colfirst = banded ? Sp->col_a + (int64_t)g * n : colend;
+      // per band [nbands][columns], touching the band's bottom edge (or, for
+      // RQA, the line of identity)
+      uint32_t* __restrict__ colfirst =
+          banded ? Sp->col_a + (int64_t)g * (XR ? ncol : n) : colend;
       uint32_t* ring_in = warp > 0 ? ring + (warp - 1) * RING * 64 : nullptr;
       uint32_t* ring_out = !leftmost ? ring + warp * RING * 64 : nullptr;
       int seq_in = 0, seq_out = 0;
@@ -585,8 +589,8 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
         }
         cst_s[c * 32 + lane] = ST_FLAG;
         // carry from below the first block: a run touching the band's bottom
-        // edge where the diagonal continues there (cell (R1, j) with j > R1)
-        dU_s[c * 32 + lane] = (cut_below && j > R1) ? DG_EDGE : 0u;
+        // edge where the diagonal continues there (cell (R1, j) exists)
+        dU_s[c * 32 + lane] = (cut_below && (XR ? j >= 0 : j > R1)) ? DG_EDGE : 0u;
       }
       int bufo = 0;  // which half of dU_s holds the carries of the block below
       ShortCounts sc{0, 0, 0, 0, 0};
@@ -794,7 +798,10 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             auto emitc = [&](uint32_t col, uint32_t len) { hs.add2(col, len); };
             auto firstc = [&](uint32_t col, uint32_t len) {
               if constexpr (XR) {
-                if (len) hs.add2(col, len);
+                if (banded && R1 < n)  // touches the band's bottom edge: join later
+                  colfirst[j] = len | (col << 31);
+                else if (len)
+                  hs.add2(col, len);
               } else {
                 colfirst[j] = len | (col << 31);
               }
@@ -905,15 +912,18 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             const uint32_t st = cst_s[c * 32 + lane];
             const uint32_t len = st & ST_LEN, col = (st >> 28) & 1u;
             const bool whole = (st & ST_FLAG) != 0;  // one run over the column's segment
-            if (!banded || (R0 == 0 && (j <= R1 || !whole))) {
+            // the run continues in the band above, or below: record it
+            const bool keep = banded && !(R0 == 0 && ((!XR && j <= R1) || !whole));
+            if (!keep) {
               if (len > 0) {
                 if (!XR && whole)
                   colfirst[j] = len | (col << 31);
                 else
                   hs.add2(col, len);
               }
-            } else {  // the run continues in the band above, or below: join later
-              Sp->col_z[(int64_t)g * n + j] = len | (whole ? (1u << 30) : 0u) | (col << 31);
+            } else {
+              Sp->col_z[(int64_t)g * (XR ? ncol : n) + j] =
+                  len | (whole ? (1u << 30) : 0u) | (col << 31);
             }
             const uint32_t du = dU_s[bufo * C * 32 + c * 32 + lane];
             dia_z[off + (j - R0) - klo] =

@@ -1,30 +1,34 @@
 // tile_cross0.cu -- cross-recurrence instantiations of the fused tile kernel
 // (two series, no symmetry fold) for norm 0
-// (0 = L-infinity, 1 = L2, 2 = L1), m = 1..10, FP32 + recheck and FP64.
+// (0 = L-infinity, 1 = L2, 2 = L1), m = 1..10, FP32 + recheck and FP64, with and
+// without row bands.
 #include "rqa_kernels.h"
 #include "rqa_tile.cuh"
 
 namespace rqa {
 
 template <int M>
-static TileFn pick(int cols, bool f64) {
+static TileFn pick(int cols, bool f64, bool bands) {
   if (cols != 4) return nullptr;
+  if (bands)
+    return f64 ? (TileFn)tile_kernel<M, 0, 4, true, true, false, true>
+               : (TileFn)tile_kernel<M, 0, 4, false, true, false, true>;
   return f64 ? (TileFn)tile_kernel<M, 0, 4, true, true>
              : (TileFn)tile_kernel<M, 0, 4, false, true>;
 }
 
-TileFn tile_kernel_cross_norm0(int m, int cols, bool f64) {
+TileFn tile_kernel_cross_norm0(int m, int cols, bool f64, bool bands) {
   switch (m) {
-    case 1: return pick<1>(cols, f64);
-    case 2: return pick<2>(cols, f64);
-    case 3: return pick<3>(cols, f64);
-    case 4: return pick<4>(cols, f64);
-    case 5: return pick<5>(cols, f64);
-    case 6: return pick<6>(cols, f64);
-    case 7: return pick<7>(cols, f64);
-    case 8: return pick<8>(cols, f64);
-    case 9: return pick<9>(cols, f64);
-    case 10: return pick<10>(cols, f64);
+    case 1: return pick<1>(cols, f64, bands);
+    case 2: return pick<2>(cols, f64, bands);
+    case 3: return pick<3>(cols, f64, bands);
+    case 4: return pick<4>(cols, f64, bands);
+    case 5: return pick<5>(cols, f64, bands);
+    case 6: return pick<6>(cols, f64, bands);
+    case 7: return pick<7>(cols, f64, bands);
+    case 8: return pick<8>(cols, f64, bands);
+    case 9: return pick<9>(cols, f64, bands);
+    case 10: return pick<10>(cols, f64, bands);
     default: return nullptr;
   }
 }

@@ -6,9 +6,9 @@ namespace rqa {
 
 TileFn tile_kernel_for(int m, int norm, int cols, bool f64, bool cross, bool bands) {
   switch (norm) {
-    case 0: return cross ? tile_kernel_cross_norm0(m, cols, f64) : tile_kernel_norm0(m, cols, f64, bands);
-    case 1: return cross ? tile_kernel_cross_norm1(m, cols, f64) : tile_kernel_norm1(m, cols, f64, bands);
-    case 2: return cross ? tile_kernel_cross_norm2(m, cols, f64) : tile_kernel_norm2(m, cols, f64, bands);
+    case 0: return cross ? tile_kernel_cross_norm0(m, cols, f64, bands) : tile_kernel_norm0(m, cols, f64, bands);
+    case 1: return cross ? tile_kernel_cross_norm1(m, cols, f64, bands) : tile_kernel_norm1(m, cols, f64, bands);
+    case 2: return cross ? tile_kernel_cross_norm2(m, cols, f64, bands) : tile_kernel_norm2(m, cols, f64, bands);
     default: return nullptr;
   }
 }

@@ -6,9 +6,10 @@
 
 namespace rqa {
 
-TileFn tile_kernel_matrix(int cols) {
+TileFn tile_kernel_matrix(int cols, bool bands) {
   if (cols != 4) return nullptr;
-  return (TileFn)tile_kernel<1, 0, 4, false, true, true>;
+  return bands ? (TileFn)tile_kernel<1, 0, 4, false, true, true, true>
+               : (TileFn)tile_kernel<1, 0, 4, false, true, true>;
 }
 
 }  // namespace rqa

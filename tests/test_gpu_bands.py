@@ -95,3 +95,64 @@ def test_automatic_bands_n20000():
     for got, k in zip(r.histograms(), ("hd", "hv", "hw")):
         assert np.array_equal(got, want[k]), k
     assert_same_measures(meas, want["measures"])
+
+
+# ---------------------------------------------------------------- cross / matrix
+def _cross_check(x, y, **kw):
+    want = oracle.cross_rqa(x, y, oracle.Settings(**kw))
+    r = gp.RQA(gpu_settings(**kw))
+    meas = r.run_cross(x, y)
+    for got, k in zip(r.histograms(), ("hd", "hv", "hw")):
+        assert np.array_equal(got, want[k]), k
+    assert_same_measures(meas, want["measures"])
+    return r.stats()
+
+
+@pytest.mark.parametrize("rows", [32, 96, 512])
+@pytest.mark.parametrize("warps", [1, 3, 8])
+@pytest.mark.parametrize("n1,n2", [(900, 2400), (2400, 900), (1000, 1000)])
+def test_cross_bands(monkeypatch, rows, warps, n1, n2):
+    monkeypatch.setenv("RQA_BAND_ROWS", str(rows))
+    monkeypatch.setenv("RQA_TILE_WARPS", str(warps))
+    x = synth.lorenz_x(n1 + 6, 800 + n1, discard=1000)
+    y = synth.lorenz_x(n2 + 6, 900 + n2, discard=1000)
+    st = _cross_check(x, y, m=4, tau=2, eps=0.6, norm=0, theiler=2)
+    assert st["band_rows"] == rows
+
+
+@pytest.mark.parametrize("w", [0, 5])
+def test_cross_bands_constant_and_same_series(monkeypatch, w):
+    monkeypatch.setenv("RQA_BAND_ROWS", "64")
+    monkeypatch.setenv("RQA_TILE_WARPS", "2")
+    _cross_check(np.full(900, 0.3), np.full(1300, 0.3), m=2, tau=1, eps=0.1, norm=1, theiler=w)
+    s = synth.ar1(1500, 5, 0.9)
+    a = gp.RQA(gpu_settings(3, 1, 0.5, 1, w))
+    ma = a.run(s)
+    b = gp.RQA(gpu_settings(3, 1, 0.5, 1, w))
+    mb = b.run_cross(s, s)
+    for u, v in zip(a.histograms(), b.histograms()):
+        assert np.array_equal(u, v)
+    assert_same_measures(mb, ma)
+
+
+@pytest.mark.parametrize("rows", [32, 160])
+def test_matrix_bands(monkeypatch, rows):
+    monkeypatch.setenv("RQA_BAND_ROWS", str(rows))
+    rng = np.random.default_rng(rows)
+    for R in (np.ones((1300, 1700), np.uint8),
+              (rng.random((1700, 1100)) < 0.5).astype(np.uint8),
+              ((np.arange(1300)[None, :] - np.arange(900)[:, None]) % 3 == 0).astype(np.uint8)):
+        want = oracle.matrix_rqa(R, oracle.Settings(m=1, tau=1, eps=1.0, norm=0, theiler=1))
+        r = gp.RQA(gpu_settings(1, 1, 1.0, 0, 1))
+        meas = r.run_matrix(R)
+        for got, k in zip(r.histograms(), ("hd", "hv", "hw")):
+            assert np.array_equal(got, want[k]), k
+        assert_same_measures(meas, want["measures"])
+        assert r.stats()["band_rows"] == rows
+
+
+def test_cross_automatic_bands():
+    x = synth.ar1(20_000, 71, 0.9)
+    y = synth.ar1(15_000, 72, 0.9)
+    st = _cross_check(x, y, m=3, tau=1, eps=0.4, norm=1, theiler=0)
+    assert st["band_rows"] > 0
