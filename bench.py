@@ -11,10 +11,14 @@ L2 is flushed (a 512 MiB write) before every timed step.
 
 Also reported on the same line: end-to-end cells/s through the C ABI with
 host buffers (copies inside the timed region), the FP64-everywhere GPU path
-on the same series, the batched workload (4,096 uneven series, one graph per
-call) against sequential single-series calls, the served workload (Poisson
-arrivals, p50 / p99 latency), the clocks seen during the timed region, and
-the FP64 CPU oracle timed on a bounded sample on the host's cores.
+on the same series, cross recurrence of two 524,288-point series, line
+detection over a 32,768 x 32,768 precomputed bit matrix, an 8,192 x 8,192
+recurrence-plot window, the paper's own sine workload end to end (Sect. 8.2,
+with the paper's runtimes as context), the batched workload (4,096 uneven
+series, one graph per call) against sequential single-series calls, the
+served workload (Poisson arrivals, p50 / p99 latency), the clocks seen during
+the timed region, and the FP64 CPU oracle timed on a bounded sample on the
+host's cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
