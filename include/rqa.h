@@ -290,6 +290,16 @@ int rqa_autotune(const rqa_settings* settings, const double* host_series,
                  float* ms_per_width);
 void rqa_autotune_clear(void);
 const char* rqa_autotune_last_error(void);
+/* ------------------------------------------------------ failure self-test
+ * The paper has no counterpart.  The tile kernel's warps hand carries to
+ * each other through bounded waits (about 2 s of SM clock); a wait that runs
+ * out raises an abort flag and the series fails with RQA_ETIMEOUT instead of
+ * hanging the GPU.  rqa_selftest_bounded_wait() exercises exactly that wait
+ * on a counter that nothing raises: *status receives the status the waiting
+ * warp reported (RQA_ETIMEOUT when the mechanism works) and *cycles_waited
+ * the SM cycles it waited.  Returns RQA_OK if the wait gave up and raised the
+ * abort flag; the CUDA context stays usable afterwards. */
+int rqa_selftest_bounded_wait(int32_t* status, int64_t* cycles_waited);
 /* ----------------------------------------------------------------- batched
  * Many independent series in one submission: the work of all series is one
  * queue of (series, strip) items processed by persistent CTAs, one launch

@@ -11,6 +11,7 @@
 
 #include "../../include/rqa.h"
 #include "rqa_engine.h"
+#include "rqa_kernels.h"
 
 struct rqa_handle {
   rqa_settings st{};
@@ -231,6 +232,31 @@ int rqa_batch_create(rqa_batch** out) {
   }
   *out = b;
   return RQA_OK;
+}
+
+int rqa_selftest_bounded_wait(int32_t* status, int64_t* cycles_waited) {
+  std::string msg;
+  int dev = 0;
+  int rc = find_device(&dev, &msg);
+  if (rc != RQA_OK) return rc;
+  unsigned long long* d = nullptr;
+  unsigned long long h[3] = {0, 0, 0};
+  cudaError_t e = cudaMalloc(&d, sizeof(h));
+  if (e != cudaSuccess) return RQA_ENOMEM;
+  rc = RQA_OK;
+  if ((e = cudaMemset(d, 0, sizeof(h))) != cudaSuccess) {
+    rc = RQA_ECUDA;
+  } else {
+    rqa::launch_wait_selftest(d, nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      rc = RQA_ECUDA;
+  }
+  cudaFree(d);
+  if (rc != RQA_OK) return rc;
+  if (status) *status = static_cast<int32_t>(h[0]);
+  if (cycles_waited) *cycles_waited = static_cast<int64_t>(h[1]);
+  return h[2] == 1 ? RQA_OK : RQA_ECUDA;  // the abort flag must be raised
 }
 
 int rqa_batch_run(rqa_batch* b, const rqa_settings* settings, const double* const* series,

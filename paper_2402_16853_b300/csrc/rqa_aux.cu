@@ -562,6 +562,32 @@ void launch_plot(const SeriesDesc* d_sd, int64_t i0, int64_t j0, int64_t rows, i
   plot_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_sd, i0, j0, rows, cols, out, f64);
 }
 
+// ------------------------------------------------------ bounded-wait test
+// Failure detection without a fault: warp 1 waits, with the tile kernel's
+// own bounded spin, for a counter that warp 0 never raises.  The wait must
+// give up after SPIN_CYCLES, raise the abort flag and report RQA_ETIMEOUT
+// (status[0]) with the cycles it waited (status[1]); the context stays usable.
+__global__ void wait_selftest_kernel(unsigned long long* status) {
+  __shared__ volatile int ctr;
+  __shared__ volatile int abort_flag;
+  if (threadIdx.x == 0) {
+    ctr = 0;
+    abort_flag = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 32) {
+    const long long t0 = clock64();
+    const bool ok = spin_until_ge(&ctr, 1, &abort_flag);
+    status[0] = ok ? 0ull : 6ull /* RQA_ETIMEOUT */;
+    status[1] = (unsigned long long)(clock64() - t0);
+    status[2] = abort_flag ? 1ull : 0ull;
+  }
+}
+
+void launch_wait_selftest(unsigned long long* status, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 64, 0, st>>>(status);
+}
+
 // ------------------------------------------------------------ host launch
 void launch_prepare(SeriesDesc* d_sd, int count, cudaStream_t st) {
   prepare_kernel<<<count, 256, 0, st>>>(d_sd);

@@ -138,6 +138,7 @@ def load(path: str = LIB_PATH):
         "rqa_autotune": (c.c_int, [P(_CSettings), P(c.c_double), c.c_int64, c.c_int32,
                                    P(c.c_int32), P(c.c_float)]),
         "rqa_autotune_clear": (None, []),
+        "rqa_selftest_bounded_wait": (c.c_int, [P(c.c_int32), P(c.c_int64)]),
         "rqa_autotune_last_error": (c.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -496,6 +497,18 @@ def autotune(settings: Settings, n_points: Optional[int] = None, series=None,
     if rc:
         raise RQAError(rc, "rqa_autotune", load().rqa_autotune_last_error().decode())
     return {"warps": best.value, "ms": {w: ms[q] for q, w in enumerate((1, 2, 4, 8))}}
+
+
+def selftest_bounded_wait():
+    """Run the bounded-wait self-test: returns (status the waiting warp
+    reported -- 6, RQA_ETIMEOUT, when the mechanism works -- and the SM
+    cycles it waited).  Raises RQAError if the wait did not give up."""
+    st = ctypes.c_int32()
+    cyc = ctypes.c_int64()
+    rc = load().rqa_selftest_bounded_wait(ctypes.byref(st), ctypes.byref(cyc))
+    if rc:
+        raise RQAError(rc, "rqa_selftest_bounded_wait")
+    return st.value, cyc.value
 
 
 def autotune_clear() -> None:

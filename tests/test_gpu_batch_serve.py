@@ -171,3 +171,32 @@ def _oversized_and_cancel(srv):
         assert rc == 0
     if rel == 0:
         assert srv.poll(ts[-1])[0] == 10   # forgotten
+
+
+def test_served_banded_requests_equal_alone():
+    """Requests of 70,000 points run in row bands in the server's epochs (and
+    alone); results must equal the oracle and the single runs."""
+    big = [synth.ar1(70_000, 41 + k, 0.9) for k in range(2)]
+    small, eps_small = synth.make_series([synth.draw_spec(np.random.default_rng(7), 3000)
+                                          for _ in range(6)], 8)
+    settings = [gp.Settings(m=3, tau=1, eps=0.4, norm=1, theiler=1) for _ in big]
+    settings += [gp.Settings(m=2, tau=1, eps=e, norm=0, theiler=1) for e in eps_small]
+    series = big + small
+    alone = []
+    for stg, s in zip(settings, series):
+        r = gp.RQA(stg)
+        alone.append(r.run(s))
+        if len(s) >= 70_000:
+            assert r.stats()["band_rows"] > 0
+    want = oracle.rqa(big[0], oracle.Settings(m=3, tau=1, eps=0.4, norm=1, theiler=1),
+                      mode="streaming")
+    assert_same_measures(alone[0], want["measures"])
+    srv = gp.Server(8 << 30, max_slots=8)
+    try:
+        ts = [srv.submit(stg, s) for stg, s in zip(settings, series)]
+        for t, a in zip(ts, alone):
+            rc, m = srv.wait(t, 120_000)
+            assert rc == 0
+            assert_same_measures(m, a)
+    finally:
+        srv.close()
