@@ -276,7 +276,14 @@ def run_mine(args):
     ops_per_pair = 2 * params["m"] + 1
     k_ms = float(np.mean(kernel_ms))
     achieved = pairs * ops_per_pair / (k_ms / 1e3) / 1e12
-    peak = sms * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    peak_theory = sms * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    # measured FP32 issue throughput of the distance loop's operations; the
+    # roofline divides by the larger of theory and measurement
+    try:
+        probes = {k: v / 1e12 for k, v in gp.probe_alu().items()}
+    except gp.RQAError:
+        probes = {}
+    peak = max([peak_theory] + list(probes.values()))
     traffic = tile_traffic(n)
 
     # ---- end to end through the C ABI with host buffers
@@ -357,8 +364,13 @@ def run_mine(args):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "tile_kernel<3,L2,4,fp32>", "kernel_ms": k_ms,
                      "ops_per_pair": ops_per_pair, "pairs_per_launch": pairs,
-                     "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} "
-                                   f"MHz ({peak_kind} sm_max_mhz)"},
+                     "peak_basis": f"max of {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                   f"{sm_max:.0f} MHz ({peak_kind} sm_max_mhz) = "
+                                   f"{peak_theory:.2f} TOP/s and the measured probes",
+                     "peak_probes_tops": probes,
+                     "frac_of_theory_at_run_clock": (
+                         achieved / (peak_theory * clk["sm_mhz"] / sm_max)
+                         if clk.get("sm_mhz") else None)},
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,

@@ -300,6 +300,15 @@ const char* rqa_autotune_last_error(void);
  * the SM cycles it waited.  Returns RQA_OK if the wait gave up and raised the
  * abort flag; the CUDA context stays usable afterwards. */
 int rqa_selftest_bounded_wait(int32_t* status, int64_t* cycles_waited);
+/* ---------------------------------------------------------- ALU probe
+ * The paper has no counterpart.  rqa_probe_alu() measures, on the current
+ * device, the throughput of one FP32 operation of the distance loop with
+ * every SM fully occupied by independent dependency chains: kind 0 fma.f32,
+ * 1 fma.f32x2, 2 add.f32, 3 sub.f32x2, 4 max.f32.  *ops_per_s counts one
+ * operation per lane (two for the packed f32x2 forms), the unit of the
+ * roofline's per-pair operation count; the benchmark divides by the larger of
+ * this and SMs x 128 lanes x clock.  Takes a few milliseconds. */
+int rqa_probe_alu(int32_t kind, double* ops_per_s);
 /* ----------------------------------------------------------------- batched
  * Many independent series in one submission: the work of all series is one
  * queue of (series, strip) items processed by persistent CTAs, one launch

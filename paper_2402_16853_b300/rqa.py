@@ -139,6 +139,7 @@ def load(path: str = LIB_PATH):
                                    P(c.c_int32), P(c.c_float)]),
         "rqa_autotune_clear": (None, []),
         "rqa_selftest_bounded_wait": (c.c_int, [P(c.c_int32), P(c.c_int64)]),
+        "rqa_probe_alu": (c.c_int, [c.c_int32, P(c.c_double)]),
         "rqa_autotune_last_error": (c.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -509,6 +510,22 @@ def selftest_bounded_wait():
     if rc:
         raise RQAError(rc, "rqa_selftest_bounded_wait")
     return st.value, cyc.value
+
+
+ALU_PROBES = ("fma.f32", "fma.f32x2", "add.f32", "sub.f32x2", "max.f32")
+
+
+def probe_alu() -> dict:
+    """Measured FP32 operations/s of each probe kind (one per lane, two for
+    the packed f32x2 forms) on the current device."""
+    res = {}
+    for k, name in enumerate(ALU_PROBES):
+        v = ctypes.c_double()
+        rc = load().rqa_probe_alu(k, ctypes.byref(v))
+        if rc:
+            raise RQAError(rc, "rqa_probe_alu")
+        res[name] = v.value
+    return res
 
 
 def autotune_clear() -> None:

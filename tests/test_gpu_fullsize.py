@@ -2,9 +2,11 @@
 
 * Lorenz-x, N = 100,000 (n = 99,988, max norm, w = 5): all histograms and
   measures bit-exact against the streaming FP64 oracle.
-* AR(1), N = 1,048,576 (n = 1,048,574, L2, w = 1): too large for the oracle,
-  so it is checked by properties that hold at any size and by sampled
-  decisions:
+* AR(1), N = 1,048,576 (n = 1,048,574, L2, w = 1): the oracle's complete
+  result, computed once on 16 host cores by tests/golden/make_ar1_n1m_oracle.py
+  and stored as SHA-256 digests of the three histograms plus the measures,
+  must match bit for bit; besides, properties that hold at any size and
+  sampled decisions:
   - the diagonal scan and the column / row scans see the same recurrence
     points (sum l P_D(l) == sum l P_V(l)), and white lines cover the rest of
     the n^2 cells;
@@ -16,6 +18,10 @@
   tau = 2, eps = 1, no Theiler window): the line of identity is one line of
   length n, and the diagonal histogram is otherwise even (both triangles).
 """
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -46,6 +52,23 @@ def ar1_full():
     r = gp.RQA(gp.Settings(**p))
     meas = r.run(s)
     return s, p, r, meas, r.histograms(), r.stats()
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ar1_n1m_oracle.json")
+
+
+def test_ar1_n1m_equals_full_oracle(ar1_full):
+    s, p, r, meas, (hd, hv, hw), st = ar1_full
+    gold = json.load(open(GOLDEN))
+    assert gold["n_vec"] == st["n_vec"] and gold["params"] == p
+    for name, h in (("hd", hd), ("hv", hv), ("hw", hw)):
+        g = gold[name]
+        assert int(h.sum()) == g["sum"], name
+        assert {str(l): int(h[l]) for l in range(1, 65) if h[l]} == g["head"], name
+        assert hashlib.sha256(np.ascontiguousarray(h, dtype="<u8").tobytes()).hexdigest() \
+            == g["sha256"], name
+    assert meas["recurrence_points"] == gold["rp"]
+    assert_same_measures(meas, gold["measures"])
 
 
 def test_ar1_n1m_invariants(ar1_full):

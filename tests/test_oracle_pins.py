@@ -344,3 +344,21 @@ def test_table3_lmax_is_n_without_theiler_window():
         ms = r["measures"]
         assert r["n"] == g["l_max"] == ms["l_max"]
         assert round(ms["div"], g["div_print_decimals"]) == g["div_printed"]
+
+
+def test_full_size_golden_is_consistent():
+    """The stored full-size oracle result (AR(1), n = 1,048,574, w = 1) obeys
+    the invariants of any recurrence matrix: every recurrence point lies on
+    one diagonal and one vertical line, white lines fill the remaining
+    cells, the two triangles mirror each other, and the measures follow from
+    the histograms' stored totals."""
+    path = os.path.join(GOLDEN, "ar1_n1m_oracle.json")
+    g = json.load(open(path))
+    n, rp = g["n_vec"], g["rp"]
+    assert n == 1_048_574
+    assert g["hd"]["weighted_sum"] == rp == g["hv"]["weighted_sum"]
+    assert g["hw"]["weighted_sum"] == n * n - rp
+    assert g["hd"]["sum"] % 2 == 0            # w = 1: mirrored triangles
+    assert g["measures"]["recurrence_points"] == rp
+    assert g["measures"]["rr"] == rp / (n * n)
+    assert g["measures"]["l_max"] == g["hd"]["max_len"]
