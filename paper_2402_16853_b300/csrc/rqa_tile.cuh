@@ -28,6 +28,17 @@
 // that touches the line of identity is stored apart and joined by the
 // finalize kernel.  Counts go to shared-memory histograms flushed once per
 // strip.
+//
+// Template flags select the variants built from this one body:
+//   XR  cross recurrence (Sect. 3.3): rows from one series, columns from
+//       another, every strip spans all rows, no row scans and no
+//       line-of-identity join, a two-sided Theiler window;
+//   MX  a precomputed matrix (Sect. 9): the recurrence words are read from
+//       the caller's bits instead of computed (with XR);
+//   BD  row bands: a work item is (strip, band of rows), so series whose
+//       strips alone cannot fill the GPU still do; column runs and diagonals
+//       that cross a band edge get their own descriptors.  A separate
+//       instantiation, so the unbanded kernel keeps its registers.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
