@@ -78,6 +78,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(seconds: float, dist, device) -> float:
+    """The job's time: the maximum of a per-rank time over all ranks (the
+    rank itself when not distributed)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: float, world: int, steps: int, seconds: float) -> float:
+    """Units all ranks processed per second of the job's time (every rank
+    runs the same workload: weak scaling, replicas)."""
+    return world * units_per_rank_step * steps / seconds
+
+
 def measured_peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -262,16 +279,12 @@ def run_mine(args):
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    if dist is not None:
-        tt = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, dev)
     barrier()
     meas = r.measures()
     stt = r.stats()
     cells = float(n) * n
-    value = world * cells * args.steps / elapsed
+    value = whole_job_rate(cells, world, args.steps, elapsed)
     pairs = stt["pairs"]
     ops_per_pair = 2 * params["m"] + 1
     k_ms = float(np.mean(kernel_ms))
