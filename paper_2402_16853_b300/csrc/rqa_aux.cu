@@ -94,9 +94,17 @@ __global__ void prepare_kernel(SeriesDesc* __restrict__ sd) {
     bound = 2.02 * (3.0 * u * E + 2.0 * u * Ms) + 4.0 * 0x1p-52 * E;
   }
   double band = fmax(1e-5 * unit, bound);
+  // The FP64 definition itself leaves the normal range when the squares or
+  // sums of the differences (at most 2 dev each) overflow, or when squares or
+  // sums of radius-sized differences underflow; there the scaled FP32 test
+  // could decide a pair differently from it, so every pair is re-decided.
+  const double span = 2.0 * dev;
+  const bool fp64_range = S.norm == 1   ? (span > 1e150 / sm || S.eps < 1e-140)
+                          : S.norm == 2 ? (span * m > 1e300 || S.eps < 1e-290)
+                                        : span > 1e300;
   if (S.band_override >= 0.0)
     band = S.band_override * unit;
-  else if (bound >= 0.25 * unit)
+  else if (bound >= 0.25 * unit || fp64_range)
     band = INFINITY;  // the FP32 test would decide almost nothing: re-decide all
   float thr;
   if (S.norm == 1) {

@@ -166,3 +166,14 @@ def test_sampled_decisions_match_oracle():
     got = r.sample(i, j)
     R, _ = oracle.matrix(s, oracle.Settings(**p))
     assert np.array_equal(got, R[i, j])
+
+
+@pytest.mark.parametrize("norm", [0, 1, 2])
+@pytest.mark.parametrize("scale", [1e200, 1e-200, 1e-305, 1e305])
+def test_extreme_magnitudes(norm, scale):
+    """Values whose FP64 squares or sums overflow or underflow: the library
+    re-decides every pair in FP64 so the decisions stay the definition's."""
+    s = synth.ar1(500, 31, 0.9) * scale
+    eps = 0.5 * scale
+    r, st, want = check_parity(s, m=3, tau=1, eps=eps, norm=norm, theiler=1)
+    assert st["exact"] == 1
