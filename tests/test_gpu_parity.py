@@ -177,3 +177,30 @@ def test_extreme_magnitudes(norm, scale):
     eps = 0.5 * scale
     r, st, want = check_parity(s, m=3, tau=1, eps=eps, norm=norm, theiler=1)
     assert st["exact"] == 1
+
+
+@pytest.mark.parametrize("w", [0, 1])
+def test_all_white_tiny_radius(w):
+    """A radius below every distance: only the line of identity (w = 0) can
+    recur; every column is white otherwise."""
+    s = synth.ar1(1500, 17, 0.9)
+    r, st, want = check_parity(s, m=2, tau=1, eps=1e-12, norm=1, theiler=w)
+    n = len(s) - 1
+    assert want["rp"] == (n if w == 0 else 0)
+
+
+@pytest.mark.parametrize("norm", [0, 1, 2])
+@pytest.mark.parametrize("m", [1, 2])
+def test_pairs_within_ulps_of_radius(norm, m):
+    """Neighbouring values spaced eps plus a few units in the last place, so
+    that many pairs sit within a handful of ulps of the radius on both
+    sides; the FP32 test must hand all of them to the FP64 recheck."""
+    rng = np.random.default_rng(m * 3 + norm)
+    eps = 0.3125
+    ulp = np.spacing(eps)
+    steps = eps + ulp * rng.integers(-3, 4, 3000)
+    s = np.cumsum(steps) * rng.choice([1.0, -1.0], 3000).cumprod()  # zig-zag walk
+    s = np.concatenate([[0.0], s])
+    e = eps * (m if norm == 2 else (m ** 0.5 if norm == 1 else 1.0))
+    r, st, want = check_parity(s, m=m, tau=1, eps=e, norm=norm, theiler=1)
+    assert st["rechecks"] > 0

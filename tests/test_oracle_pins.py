@@ -362,3 +362,17 @@ def test_full_size_golden_is_consistent():
     assert g["measures"]["recurrence_points"] == rp
     assert g["measures"]["rr"] == rp / (n * n)
     assert g["measures"]["l_max"] == g["hd"]["max_len"]
+
+
+@pytest.mark.parametrize("norm", NORMS)
+@pytest.mark.parametrize("m,tau", [(1, 1), (3, 2)])
+def test_time_reversal_on_dyadic_data(norm, m, tau):
+    """Reversing the series maps x_i to x_{n-1-i} with its coordinates in
+    reverse order, i.e. rotates the matrix by 180 degrees; on dyadic data
+    every distance is exact, so all three histograms are unchanged."""
+    s = synth.dyadic(700, 9, levels=6, scale_log2=-2)
+    st = Settings(m=m, tau=tau, eps=0.75, norm=norm, theiler=1)
+    a = oracle.rqa(s, st)
+    b = oracle.rqa(s[::-1].copy(), st)
+    for k in ("hd", "hv", "hw"):
+        assert np.array_equal(a[k], b[k]), k
