@@ -94,16 +94,16 @@ struct Sizes {
 // Row-band height: RQA_BAND_ROWS if set (rounded up to a multiple of 32; for
 // tests and tuning), else bands only when the strips alone give fewer than
 // 7,104 warps (two per resident warp slot of the 80-register kernel on 148
-// SMs) -- about 2,048 items of at least 1,024 rows.  `rows` is the number of
+// SMs) -- about 2,048 items of at least 128 rows.  `rows` is the number of
 // rows summed over the strips.
 int64_t band_rows_for(int64_t n, int64_t rows, int64_t nstrips, int warps) {
   if (const char* e = std::getenv("RQA_BAND_ROWS")) {
     const int64_t h = std::atoll(e);
     return h > 0 ? (h + 31) / 32 * 32 : 0;
   }
-  if (n < 8192 || nstrips * warps >= 7104) return 0;
+  if (n < 512 || nstrips * warps >= 7104) return 0;
   const int64_t h = (rows + 2047) / 2048;
-  return std::max<int64_t>(1024, (h + 31) / 32 * 32);
+  return std::max<int64_t>(128, (h + 31) / 32 * 32);
 }
 
 // Visit the items (Q, g) of a banded series with the rows they hold and the
