@@ -187,6 +187,78 @@ Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross 
   return z;
 }
 
+// Validation of one input beyond its settings: pointers, lengths, limits.
+int validate_input(const SeriesInput& in, std::string* msg) {
+  int s = validate_settings(&in.st, msg);
+  if (s != RQA_OK) return s;
+  if (in.matrix) {  // a precomputed matrix: N rows, N2 columns
+    if (!in.bits_host && !in.bits_dev) {
+      *msg = "matrix pointer is NULL";
+      return RQA_EINVAL;
+    }
+    if (in.N < 1 || in.N2 < 1) {
+      *msg = "matrix has no rows or no columns";
+      return RQA_ESHORT;
+    }
+    if (in.N > RQA_MAX_N || in.N2 > RQA_MAX_N) {
+      *msg = "more than RQA_MAX_N rows or columns";
+      return RQA_ETOOBIG;
+    }
+    return RQA_OK;
+  }
+  if (!in.host && !in.dev) {
+    *msg = "series pointer is NULL";
+    return RQA_EINVAL;
+  }
+  if (in.N < 1) {
+    *msg = "series is empty";
+    return RQA_ESHORT;
+  }
+  if (nvec_of(in.st, in.N) < 1) {
+    *msg = "series shorter than the embedding window (m-1)*tau + 1";
+    return RQA_ESHORT;
+  }
+  if (nvec_of(in.st, in.N) > RQA_MAX_N) {
+    *msg = "more than RQA_MAX_N embedded vectors";
+    return RQA_ETOOBIG;
+  }
+  if (in.cross) {
+    if (!in.host2 && !in.dev2) {
+      *msg = "second series pointer is NULL";
+      return RQA_EINVAL;
+    }
+    if (in.N2 < 1 || nvec_of(in.st, in.N2) < 1) {
+      *msg = "second series shorter than the embedding window (m-1)*tau + 1";
+      return RQA_ESHORT;
+    }
+    if (nvec_of(in.st, in.N2) > RQA_MAX_N) {
+      *msg = "more than RQA_MAX_N embedded vectors in the second series";
+      return RQA_ETOOBIG;
+    }
+  }
+  return RQA_OK;
+}
+
+// Kernel classes onto side streams: longest work first, each class to the
+// least loaded of `nside` streams (-1: the main stream, when nside is 0).
+void assign_streams(const std::vector<double>& work, int nside, std::vector<int>& order,
+                    std::vector<int>& stream_of) {
+  const int ncls = static_cast<int>(work.size());
+  order.resize(ncls);
+  stream_of.assign(ncls, -1);
+  for (int c = 0; c < ncls; ++c) order[c] = c;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  if (nside == 0) return;
+  std::vector<double> load(nside, 0.0);
+  for (int c : order) {
+    int best = 0;
+    for (int k = 1; k < nside; ++k)
+      if (load[k] < load[best]) best = k;
+    stream_of[c] = best;
+    load[best] += work[c];
+  }
+}
+
 }  // namespace
 
 int validate_settings(const rqa_settings* st, std::string* msg) {
@@ -385,52 +457,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   bool any_fp32 = false, any_sym = false, any_cross = false, any_bands = false;
   for (int q = 0; q < count; ++q) {
     std::string msg;
-    int s = validate_settings(&in[q].st, &msg);
-    if (in[q].matrix) {  // a precomputed matrix: N rows, N2 columns
-      if (s == RQA_OK && !in[q].bits_host && !in[q].bits_dev) {
-        s = RQA_EINVAL;
-        msg = "matrix pointer is NULL";
-      } else if (s == RQA_OK && (in[q].N < 1 || in[q].N2 < 1)) {
-        s = RQA_ESHORT;
-        msg = "matrix has no rows or no columns";
-      } else if (s == RQA_OK && (in[q].N > RQA_MAX_N || in[q].N2 > RQA_MAX_N)) {
-        s = RQA_ETOOBIG;
-        msg = "more than RQA_MAX_N rows or columns";
-      }
-      if (s != RQA_OK) {
-        results[q].status = s;
-        if (count == 1) return fail(s, msg);
-        continue;
-      }
-    }
-    if (!in[q].matrix && s == RQA_OK && !in[q].host && !in[q].dev) {
-      s = RQA_EINVAL;
-      msg = "series pointer is NULL";
-    }
-    if (!in[q].matrix && s == RQA_OK && in[q].N < 1) {
-      s = RQA_ESHORT;
-      msg = "series is empty";
-    }
-    if (!in[q].matrix && s == RQA_OK && nvec_of(in[q].st, in[q].N) < 1) {
-      s = RQA_ESHORT;
-      msg = "series shorter than the embedding window (m-1)*tau + 1";
-    }
-    if (!in[q].matrix && s == RQA_OK && nvec_of(in[q].st, in[q].N) > RQA_MAX_N) {
-      s = RQA_ETOOBIG;
-      msg = "more than RQA_MAX_N embedded vectors";
-    }
-    if (!in[q].matrix && s == RQA_OK && in[q].cross) {
-      if (!in[q].host2 && !in[q].dev2) {
-        s = RQA_EINVAL;
-        msg = "second series pointer is NULL";
-      } else if (in[q].N2 < 1 || nvec_of(in[q].st, in[q].N2) < 1) {
-        s = RQA_ESHORT;
-        msg = "second series shorter than the embedding window (m-1)*tau + 1";
-      } else if (nvec_of(in[q].st, in[q].N2) > RQA_MAX_N) {
-        s = RQA_ETOOBIG;
-        msg = "more than RQA_MAX_N embedded vectors in the second series";
-      }
-    }
+    const int s = validate_input(in[q], &msg);
     if (s != RQA_OK) {
       results[q].status = s;
       if (count == 1) return fail(s, msg);
@@ -736,28 +763,14 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   // Classes run on up to kAux side streams so that small classes overlap
   // (their CTAs never wait on each other); the longest work goes first, each
   // class to the least loaded stream.  One class runs on the main stream.
-  std::vector<int> cls_order(ncls), cls_stream(ncls, -1);
+  std::vector<int> cls_order, cls_stream;
   const int nside = ncls > 1 ? std::min(ncls, kAux) : 0;
   {
     std::vector<double> work(ncls, 0.0);
-    for (int q = 0; q < count; ++q) {
-      const P& p = plan[q];
-      if (!p.run) continue;
-      work[p.cls] += static_cast<double>(p.z.n) * static_cast<double>(p.z.n2);
-    }
-    for (int c = 0; c < ncls; ++c) cls_order[c] = c;
-    std::stable_sort(cls_order.begin(), cls_order.end(),
-                     [&](int a, int b) { return work[a] > work[b]; });
-    std::vector<double> load(std::max(nside, 1), 0.0);
-    for (int c : cls_order) {
-      int best = 0;
-      for (int k = 1; k < nside; ++k)
-        if (load[k] < load[best]) best = k;
-      if (nside) {
-        cls_stream[c] = best;
-        load[best] += work[c];
-      }
-    }
+    for (int q = 0; q < count; ++q)
+      if (plan[q].run)
+        work[plan[q].cls] += static_cast<double>(plan[q].z.n) * static_cast<double>(plan[q].z.n2);
+    assign_streams(work, nside, cls_order, cls_stream);
   }
   // timing events are external nodes when captured, so replays record them
   const unsigned evflags = use_graph ? cudaEventRecordExternal : cudaEventRecordDefault;
