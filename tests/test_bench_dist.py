@@ -35,7 +35,7 @@ def _rank(rank, world, port, out):
 
 def test_two_gloo_ranks_agree_on_max_time_and_rate():
     world = 2
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.start_processes(_rank, args=(world, _free_port(), out), nprocs=world,
                            start_method="spawn", join=True)
