@@ -561,8 +561,113 @@ __global__ void plot_kernel(const SeriesDesc* __restrict__ sd, int64_t i0, int64
   }
 }
 
+// Bits [0, k) set, k clamped to [0, 32].
+__device__ __forceinline__ uint32_t lowmask64(int64_t k) {
+  return k <= 0 ? 0u : k >= 32 ? FULL : ((1u << k) - 1u);
+}
+
+// The FP32 path of the plot, one warp per 32 x 32 tile of the window: lane l
+// holds column j0 + 32 w + l's vector, row t's vector is broadcast from lane
+// t, the margins (in sample_one()'s operation order, so the recheck band
+// holds) give one column word per lane, pairs inside the band are re-decided
+// in FP64, and a warp transpose turns the column words into the plot's row
+// words (lane t writes row t's word w).
+template <int M, int NORM>
+__global__ void plot_tile_kernel(const SeriesDesc* __restrict__ sd, int64_t i0, int64_t j0,
+                                 int64_t rows, int64_t cols, uint32_t* __restrict__ out) {
+  const SeriesDesc& S = sd[0];
+  const int lane = threadIdx.x & 31;
+  const int64_t wpr = (cols + 31) / 32, tr = (rows + 31) / 32;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float* xe2 = S.cross ? S.xe2 : S.xe;
+  const double* s2 = S.cross ? S.s2 : S.s;
+  for (int64_t tile = warp0; tile < tr * wpr; tile += nwarps) {
+    const int64_t rb = (tile / wpr) * 32, w = tile % wpr;
+    const int64_t j = j0 + w * 32 + lane;       // this lane's column
+    const int64_t ir = i0 + rb + lane;          // the row this lane broadcasts
+    const bool jok = w * 32 + lane < cols && j >= 0 && j < S.n2;
+    const bool iok = rb + lane < rows && ir >= 0 && ir < S.n;
+    float xc[M], xr[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      xc[k] = jok ? xe2[j * S.mp + k] : 0.f;
+      xr[k] = iok ? S.xe[ir * S.mp + k] : 0.f;
+    }
+    uint32_t word = 0, near = 0;
+#pragma unroll 4
+    for (int t = 0; t < 32; ++t) {
+      float acc;
+      if (NORM == 1) {
+        acc = S.thr;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          const float d = __fsub_rn(__shfl_sync(FULL, xr[k], t), xc[k]);
+          acc = __fmaf_rn(-d, d, acc);
+        }
+      } else if (NORM == 2) {
+        acc = S.thr;
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+          acc = __fsub_rn(acc, fabsf(__fsub_rn(__shfl_sync(FULL, xr[k], t), xc[k])));
+      } else {
+        float mx = 0.f;
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+          mx = fmaxf(mx, fabsf(__fsub_rn(__shfl_sync(FULL, xr[k], t), xc[k])));
+        acc = __fsub_rn(S.thr, mx);
+      }
+      word |= (uint32_t)(!(__float_as_uint(acc) >> 31)) << t;
+      near |= (uint32_t)(fabsf(acc) <= S.band) << t;
+    }
+    // rows outside the window or the matrix, and the Theiler window: the rows
+    // i = base + t with |i - j| < w are t in [j - w + 1 - base, j + w - base)
+    const int64_t base = i0 + rb;
+    const int64_t rlim = rows - rb < S.n - base ? rows - rb : S.n - base;
+    uint32_t live = jok ? lowmask64(rlim) : 0u;
+    if (S.w > 0) live &= ~(lowmask64(j + S.w - base) & ~lowmask64(j - S.w + 1 - base));
+    word &= live;
+    near &= live;
+    while (near) {  // rare: re-decide in FP64 with the definition's order
+      const int t = __ffs(near) - 1;
+      near &= near - 1;
+      const bool r = exact_decision2<NORM>(S.s, s2, i0 + rb + t, j, M, S.tau, S.eps);
+      word = r ? (word | (1u << t)) : (word & ~(1u << t));
+    }
+    const uint32_t rw = transpose32(word, lane);  // lane t: row rb + t, bit l = column l
+    if (rb + lane < rows) out[(rb + lane) * wpr + w] = rw;
+  }
+}
+
+template <int NORM>
+static void launch_plot_tile(int m, const SeriesDesc* d_sd, int64_t i0, int64_t j0,
+                             int64_t rows, int64_t cols, uint32_t* out, unsigned blocks,
+                             cudaStream_t st) {
+  switch (m) {
+#define RQA_PLOT_CASE(MM) \
+  case MM: plot_tile_kernel<MM, NORM><<<blocks, 256, 0, st>>>(d_sd, i0, j0, rows, cols, out); break;
+    RQA_PLOT_CASE(1) RQA_PLOT_CASE(2) RQA_PLOT_CASE(3) RQA_PLOT_CASE(4) RQA_PLOT_CASE(5)
+    RQA_PLOT_CASE(6) RQA_PLOT_CASE(7) RQA_PLOT_CASE(8) RQA_PLOT_CASE(9) RQA_PLOT_CASE(10)
+#undef RQA_PLOT_CASE
+    default: break;
+  }
+}
+
 void launch_plot(const SeriesDesc* d_sd, int64_t i0, int64_t j0, int64_t rows, int64_t cols,
-                 uint32_t* out, int f64, int sms, cudaStream_t st) {
+                 uint32_t* out, int f64, int m, int norm, int sms, cudaStream_t st) {
+  if (!f64) {  // one warp per 32 x 32 tile
+    const int64_t tiles = ((rows + 31) / 32) * ((cols + 31) / 32);
+    int64_t blocks = (tiles + 7) / 8;
+    if (blocks > 16 * (int64_t)sms) blocks = 16 * (int64_t)sms;
+    if (blocks < 1) blocks = 1;
+    if (norm == 1)
+      launch_plot_tile<1>(m, d_sd, i0, j0, rows, cols, out, (unsigned)blocks, st);
+    else if (norm == 2)
+      launch_plot_tile<2>(m, d_sd, i0, j0, rows, cols, out, (unsigned)blocks, st);
+    else
+      launch_plot_tile<0>(m, d_sd, i0, j0, rows, cols, out, (unsigned)blocks, st);
+    return;
+  }
   const int64_t total = rows * ((cols + 31) / 32);
   int64_t blocks = (total + 255) / 256;
   if (blocks > 16 * (int64_t)sms) blocks = 16 * (int64_t)sms;

@@ -35,7 +35,7 @@ void launch_embed(SeriesDesc* d_sd, int count, int64_t max_n_mp, int sms, cudaSt
 int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cross, bool bands,
                   int sms, cudaStream_t st);
 void launch_plot(const SeriesDesc* d_sd, int64_t i0, int64_t j0, int64_t rows, int64_t cols,
-                 uint32_t* out, int f64, int sms, cudaStream_t st);
+                 uint32_t* out, int f64, int m, int norm, int sms, cudaStream_t st);
 // Bounded-wait self-test (status[3] in device memory: status, cycles, abort).
 void launch_wait_selftest(unsigned long long* status, cudaStream_t st);
 void launch_sample(const SeriesDesc* d_sd, const int64_t* ii, const int64_t* jj, int64_t count,

@@ -108,7 +108,8 @@ int plot_common(const rqa_settings* settings, const double* host_x, int64_t nx,
   } else {
     launch_prepare(d_sd, 1, st);
     if (!f64) launch_embed(d_sd, 1, (n + (cross ? n2 : 0)) * mp, sms, st);
-    launch_plot(d_sd, i0, j0, rows, cols, d_out, f64 ? 1 : 0, sms, st);
+    launch_plot(d_sd, i0, j0, rows, cols, d_out, f64 ? 1 : 0, settings->m, settings->norm, sms,
+                st);
     if ((e = cudaGetLastError()) != cudaSuccess ||
         (e = cudaMemcpyAsync(out_bits, d_out, out_bytes, cudaMemcpyDeviceToHost, st)) !=
             cudaSuccess ||

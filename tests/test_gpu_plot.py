@@ -43,3 +43,15 @@ def test_plot_fp64_and_ties_and_pgm(tmp_path):
     gp.write_pgm(path, got)
     data = open(path, "rb").read()
     assert data.startswith(b"P5\n399 399\n255\n") and len(data) == 15 + 399 * 399
+
+
+@pytest.mark.parametrize("m", range(1, 11))
+def test_plot_every_m(m):
+    s = synth.ar1(420 + m, 60 + m, 0.95)
+    norm = m % 3
+    eps = 0.3 * m if norm == 2 else 0.3 * (m ** 0.5 if norm == 1 else 1.0)
+    st = gp.Settings(m=m, tau=1, eps=eps, norm=norm, theiler=m % 4)
+    R, _ = oracle.matrix(s, oracle.Settings(m=m, tau=1, eps=eps, norm=norm, theiler=m % 4))
+    assert np.array_equal(gp.recurrence_plot(st, s), R)
+    assert np.array_equal(gp.recurrence_plot(st, s, i0=33, j0=5, rows=101, cols=70),
+                          R[33:134, 5:75])
