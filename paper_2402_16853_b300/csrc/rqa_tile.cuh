@@ -101,39 +101,67 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
   return x;
 }
 
-// Histogram sink: shared-memory bins for short lines, global atomics for
-// long ones.  A length outside 1..n is never written; it marks the series
-// as failed instead.
+// Histogram sink: shared-memory bins for short lines; longer ones (and any
+// length outside 1..HB-1) go to a per-warp queue in shared memory, q[0] the
+// count and q[1..OVF] the entries (type << 30 | length), which drain() moves
+// to the global histograms.  The hot path thus holds no call and no 64-bit
+// address arithmetic.  A warp adds at most three queued lengths per lane
+// between two drains (one per scan of a sub-block; lengths <= RQA_MAX_N <
+// 2^28), so 96 < OVF entries; a count above OVF is still caught by drain()
+// and reported, never written.  A length outside 1..n is never counted; it
+// marks the series as failed instead.
+constexpr int OVF = 128;
 struct HistSink {
   uint32_t* sh;              // [3][HB]
   unsigned long long* gl;    // [3][n+1]
   uint32_t n;
   unsigned long long* status;
+  uint32_t* q;               // this warp's queue: [1 + OVF]
   __device__ __forceinline__ void add(int type, uint32_t len) const {
-    if (len - 1u < (uint32_t)(HB - 1))
+    if (len - 1u < (uint32_t)(HB - 1)) {
       atomicAdd(&sh[type * HB + len], 1u);
-    else
-      slow(type, len);
+    } else {
+      const uint32_t k = atomicAdd(q, 1u);
+      if (k < (uint32_t)OVF) q[1 + k] = ((uint32_t)type << 30) | len;
+    }
   }
-  __device__ __noinline__ void slow(int type, uint32_t len) const {
-    if (len > 0 && len <= n)
-      atomicAdd(&gl[(size_t)type * (n + 1) + len], 1ull);
-    else
-      atomicExch(status, STATUS_INTERNAL);
+  // Warp-collective: move the queued lengths to the global histograms.
+  __device__ __forceinline__ void drain(int lane) const {
+    __syncwarp();
+    const uint32_t cnt = *reinterpret_cast<volatile uint32_t*>(q);
+    if (cnt == 0) return;  // the same value in every lane
+    const uint32_t m = cnt < (uint32_t)OVF ? cnt : (uint32_t)OVF;
+    for (uint32_t k = lane; k < m; k += 32) {
+      const uint32_t v = q[1 + k], type = v >> 30, len = v & 0x3FFFFFFFu;
+      if (len > 0 && len <= n)
+        atomicAdd(&gl[(size_t)type * (n + 1) + len], 1ull);
+      else
+        atomicExch(status, STATUS_INTERNAL);
+    }
+    if (cnt > (uint32_t)OVF && lane == 0) atomicExch(status, STATUS_INTERNAL);
+    __syncwarp();
+    if (lane == 0) *q = 0;
+    __syncwarp();
   }
   // vertical (black, colour 1) or white vertical (colour 0)
   __device__ __forceinline__ void add2(uint32_t colour, uint32_t len) const {
     add(colour ? HIST_VERT : HIST_WHITE, len);
+  }
+  // A run that lies inside one full 32-bit word of valid cells: 1 <= len <=
+  // 30 <= n, so its shared bin always exists and no range check is needed.
+  __device__ __forceinline__ void add_in(int type, uint32_t len) const {
+    atomicAdd(&sh[type * HB + len], 1u);
   }
 };
 
 // Scan the two-colour cells hi..lo (descending bit index) of x, continuing
 // run state st.  first(colour, len) receives the first run that ends here if
 // st carries the flag, emit(colour, len) every other run that ends here; the
-// run left open at lo is returned.
+// run left open at lo is returned.  Interior runs (cells hi..lo are valid)
+// go straight to the shared bins.
 template <class E, class F>
-__device__ __forceinline__ uint32_t scan2(uint32_t x, int hi, int lo, uint32_t st, E&& emit,
-                                          F&& first) {
+__device__ __forceinline__ uint32_t scan2(uint32_t x, int hi, int lo, uint32_t st,
+                                          const HistSink& hs, E&& emit, F&& first) {
   uint32_t cl = st & ST_LEN;
   const uint32_t cc = (st >> 28) & 1u;
   uint32_t fl = (st >> 29) & 1u;
@@ -156,7 +184,7 @@ __device__ __forceinline__ uint32_t scan2(uint32_t x, int hi, int lo, uint32_t s
     T ^= 1u << p;
     while (T) {
       p = msb(T);
-      emit(col, (uint32_t)(top - p + 1));
+      hs.add_in(col ? HIST_VERT : HIST_WHITE, (uint32_t)(top - p + 1));
       col ^= 1u;
       top = p - 1;
       T ^= 1u << p;
@@ -168,10 +196,12 @@ __device__ __forceinline__ uint32_t scan2(uint32_t x, int hi, int lo, uint32_t s
 // Scan the black runs of cells hi..lo (descending; x already restricted to
 // seg, their mask), continuing diagonal state st.  first(len) receives the
 // run that touches the strip's edge when it ends (len may be 0), emit(len)
-// every other run that ends inside.
+// every other run that ends inside (interior runs straight to the shared
+// bins: a black run consists of live cells of one word).
 template <class E, class F>
 __device__ __forceinline__ uint32_t scan_black(uint32_t x, uint32_t seg, int hi, int lo,
-                                               uint32_t st, E&& emit, F&& first) {
+                                               uint32_t st, const HistSink& hs, E&& emit,
+                                               F&& first) {
   const uint32_t z = ~x & seg;
   const uint32_t cl = st & ST_LEN;
   if (z == 0) return (cl + (uint32_t)(hi - lo + 1)) | (st & DG_EDGE);
@@ -186,7 +216,7 @@ __device__ __forceinline__ uint32_t scan_black(uint32_t x, uint32_t seg, int hi,
   while (mid) {
     const int h = msb(mid);
     const int zz = msb(z & lowmask(h));
-    emit((uint32_t)(h - zz));
+    hs.add_in(HIST_DIAG, (uint32_t)(h - zz));
     mid &= lowmask(zz);
   }
   return (uint32_t)(pbot - lo);
@@ -214,7 +244,7 @@ constexpr int FLUSH_BLOCKS = 256;
 // passed to emit / first individually.
 template <class E, class F>
 __device__ __forceinline__ uint32_t scan2_full(uint32_t x, uint32_t st, ShortCounts& sc,
-                                               E&& emit, F&& first) {
+                                               const HistSink& hs, E&& emit, F&& first) {
   const uint32_t T = (x ^ (x << 1)) & 0xFFFFFFFEu;
   uint32_t cl = st & ST_LEN;
   const uint32_t cc = (st >> 28) & 1u;
@@ -239,11 +269,10 @@ __device__ __forceinline__ uint32_t scan2_full(uint32_t x, uint32_t st, ShortCou
     sc.v3w1 += __popc(l3 & x) + (__popc(l1 & ~x) << 16);
     sc.w23 += __popc(l2 & ~x) + (__popc(l3 & ~x) << 16);
     uint32_t lg = S & ~(t1 | t2 | t3);
-    while (lg) {
+    while (lg) {  // q < ptop, so T >> (q + 1) still holds the run's upper end
       const int q = __ffs(lg) - 1;
       lg &= lg - 1;
-      const int nx = __ffs(T & ~lowmask(q + 1)) - 1;
-      emit((x >> q) & 1u, (uint32_t)(nx - q));
+      hs.add_in(((x >> q) & 1u) ? HIST_VERT : HIST_WHITE, (uint32_t)__ffs(T >> (q + 1)));
     }
   }
   return (uint32_t)(__ffs(T) - 1) | ((x & 1u) << 28);
@@ -254,7 +283,7 @@ __device__ __forceinline__ uint32_t scan2_full(uint32_t x, uint32_t st, ShortCou
 // counted by popcounts as in scan2_full.
 template <class E, class F>
 __device__ __forceinline__ uint32_t scanb_full(uint32_t x, uint32_t st, ShortCounts& sc,
-                                               E&& emit, F&& first) {
+                                               const HistSink& hs, E&& emit, F&& first) {
   const uint32_t cl = st & ST_LEN;
   if (x == FULL) return (cl + 32u) | (st & DG_EDGE);
   const int zt = msb(~x);  // highest white cell
@@ -270,11 +299,10 @@ __device__ __forceinline__ uint32_t scanb_full(uint32_t x, uint32_t st, ShortCou
     sc.d12 += __popc(Sb & t1) + (__popc(Sb & t2 & ~t1) << 16);
     sc.d3 += __popc(Sb & t3 & ~(t1 | t2));
     uint32_t lg = Sb & ~(t1 | t2 | t3);
-    while (lg) {
+    while (lg) {  // q < zt, so T >> (q + 1) still holds the run's upper end
       const int q = __ffs(lg) - 1;
       lg &= lg - 1;
-      const int nx = __ffs(T & ~lowmask(q + 1)) - 1;
-      emit((uint32_t)(nx - q));
+      hs.add_in(HIST_DIAG, (uint32_t)__ffs(T >> (q + 1)));
     }
   }
   return (uint32_t)(__ffs(~x) - 1);
@@ -458,7 +486,8 @@ inline size_t tile_smem_bytes(int warps, int row_elems, int elem_bytes, int cols
          + (size_t)warps * 32 * row_elems * elem_bytes          // row vectors
          + (size_t)warps * 4 * cols * 32 * 4                    // per-warp column state
          + (size_t)(warps > 1 ? warps - 1 : 0) * RING * 64 * 4  // carry rings
-         + (size_t)2 * warps * 4 + 16;
+         + (size_t)2 * warps * 4                                 // ring counters
+         + (size_t)warps * (OVF + 1) * 4 + 16;                  // long-line queues
 }
 
 // ------------------------------------------------------------------ kernel
@@ -484,6 +513,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
   uint32_t* ring = wstate + NW * 4 * C * 32;
   volatile int* prod = reinterpret_cast<volatile int*>(ring + (NW > 1 ? NW - 1 : 0) * RING * 64);
   volatile int* cons = prod + NW;
+  uint32_t* ovfq = reinterpret_cast<uint32_t*>(const_cast<int*>(cons) + NW) + warp * (OVF + 1);
   __shared__ int s_item;
   __shared__ int s_skip;
   __shared__ volatile int s_abort;
@@ -491,6 +521,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
   // per-lane diagonal segment masks (lane d: lower segment bits d-1..0)
   const uint32_t segL = lowmask(lane);
   const uint32_t segU = ~segL;
+  if (lane == 0) ovfq[0] = 0;
 
   for (;;) {
     __syncthreads();
@@ -548,7 +579,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
     const int wl_geo = XR ? (J1 - 1) / (32 * C) : (J1 - 2 - R0) / (32 * C);
     const int wlast = wl_geo < NW - 1 ? wl_geo : NW - 1;
     const int nh = XR ? (int)Sp->hl : n;             // longest possible line
-    const HistSink hs{sh_hist, Sp->hist, (uint32_t)nh, &Sp->counters[CNT_STATUS]};
+    const HistSink hs{sh_hist, Sp->hist, (uint32_t)nh, &Sp->counters[CNT_STATUS], ovfq};
 
     if (warp <= wlast) {
       const bool leftmost = warp == wlast;
@@ -818,9 +849,9 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
               }
             };
             if (vt == 32)
-              cst_s[c * 32 + lane] = scan2_full(R, cst_s[c * 32 + lane], sc, emitc, firstc);
+              cst_s[c * 32 + lane] = scan2_full(R, cst_s[c * 32 + lane], sc, hs, emitc, firstc);
             else if (vt > 0)
-              cst_s[c * 32 + lane] = scan2(R, vt - 1, 0, cst_s[c * 32 + lane], emitc, firstc);
+              cst_s[c * 32 + lane] = scan2(R, vt - 1, 0, cst_s[c * 32 + lane], hs, emitc, firstc);
           }
 
           // ---- operator III, lower part of full column irow = upper row irow
@@ -833,9 +864,9 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
                 row_a[roff + irow] = (uint16_t)((len << 1) | col);
               };
               if (lo <= 0)
-                rst = scan2_full(RW, rst, sc, emitr, firstr);
+                rst = scan2_full(RW, rst, sc, hs, emitr, firstr);
               else
-                rst = scan2(RW, 31, lo, rst, emitr, firstr);
+                rst = scan2(RW, 31, lo, rst, hs, emitr, firstr);
               if (lo >= 0) {  // the row ends here, at column irow + 1
                 const uint32_t len = rst & ST_LEN, col = (rst >> 28) & 1u;
                 const uint32_t same = (rst >> 29) & 1u;
@@ -857,17 +888,18 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             };
             if (c == C - 1) {
               // upper segment only (bits 31..d), entering from the right
-              dU_new[c * 32 + lane] = scan_black(D & segU, segU, 31, d, dL, emitd, firstd);
+              dU_new[c * 32 + lane] = scan_black(D & segU, segU, 31, d, dL, hs, emitd, firstd);
             } else {
               // the lower segment of sub-block c+1 (bits d-1..0 of Dprev) and
               // the upper segment of c (bits 31..d of D) are one diagonal;
               // rotated by d its cells run from bit 31 down to bit 0
               const uint32_t w = (Dprev & segL) | (D & segU);
               const uint32_t y = __funnelshift_r(w, w, d);
-              dU_new[c * 32 + lane] = scanb_full(y, dU_old[(c + 1) * 32 + lane], sc, emitd, firstd);
+              dU_new[c * 32 + lane] = scanb_full(y, dU_old[(c + 1) * 32 + lane], sc, hs, emitd, firstd);
             }
             Dprev = D;
           }
+          hs.drain(lane);
         }
         {  // the lower segment of sub-block 0 (bits d-1..0) leaves to the left
           const int k = jw0 - r0 + d - 32;
@@ -875,10 +907,12 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           dL = du;
           if (d > 0)
             dL = scan_black(
-                Dprev & segL, segL, d - 1, 0, du, [&](uint32_t len) { hs.add(HIST_DIAG, len); },
+                Dprev & segL, segL, d - 1, 0, du, hs,
+                [&](uint32_t len) { hs.add(HIST_DIAG, len); },
                 [&](uint32_t len) {
                   if (k >= klo) dia_a[off + k - klo] = (uint16_t)len;
                 });
+          hs.drain(lane);
         }
         bufo ^= 1;
         if (++since_flush == FLUSH_BLOCKS) {
@@ -942,6 +976,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           }
         }
       }
+      hs.drain(lane);
       flush_short(sc, sh_hist, lane);
     }
     __syncthreads();
