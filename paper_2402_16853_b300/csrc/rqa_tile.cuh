@@ -82,8 +82,9 @@ __device__ __forceinline__ int msb(uint32_t x) { return 31 - __clz(x); }
 
 // 32 x 32 bit transpose across a warp: lane r holds row r (bit c = A[r][c]);
 // on return lane c holds bit r = A[r][c].  Five stages; each swaps the
-// off-diagonal j x j blocks of every 2j x 2j block with one shuffle, one
-// rotate and one three-input logic operation.
+// off-diagonal j x j blocks of every 2j x 2j block with one shuffle and, for
+// j = 16 and 8, one byte permute, else one rotate and one three-input logic
+// operation.
 __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 #pragma unroll
   for (int j = 16; j >= 1; j >>= 1) {
@@ -95,10 +96,41 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
     const bool hi = (lane & j) != 0;
     const uint32_t keep = hi ? ~m : m;
     const uint32_t y = __shfl_xor_sync(FULL, x, j);
-    const uint32_t rot = __funnelshift_l(y, y, hi ? 32 - j : j);
-    x = (x & keep) | (rot & ~keep);
+    if (j >= 8) {  // whole bytes move: one byte permute of x and y
+      x = __byte_perm(x, y, j == 16 ? (hi ? 0x3276u : 0x5410u) : (hi ? 0x3715u : 0x6240u));
+    } else {
+      const uint32_t rot = __funnelshift_l(y, y, hi ? 32 - j : j);
+      x = (x & keep) | (rot & ~keep);
+    }
   }
   return x;
+}
+
+// Two independent transposes with their stages interleaved, so the shuffle
+// latencies of the two chains overlap.
+__device__ __forceinline__ void transpose32x2(uint32_t& x, uint32_t& z, int lane) {
+#pragma unroll
+  for (int j = 16; j >= 1; j >>= 1) {
+    const uint32_t m = j == 16 ? 0x0000FFFFu
+                     : j == 8  ? 0x00FF00FFu
+                     : j == 4  ? 0x0F0F0F0Fu
+                     : j == 2  ? 0x33333333u
+                               : 0x55555555u;
+    const bool hi = (lane & j) != 0;
+    const uint32_t keep = hi ? ~m : m;
+    const uint32_t y = __shfl_xor_sync(FULL, x, j);
+    const uint32_t w = __shfl_xor_sync(FULL, z, j);
+    if (j >= 8) {
+      const uint32_t sel = j == 16 ? (hi ? 0x3276u : 0x5410u) : (hi ? 0x3715u : 0x6240u);
+      x = __byte_perm(x, y, sel);
+      z = __byte_perm(z, w, sel);
+    } else {
+      const uint32_t ry = __funnelshift_l(y, y, hi ? 32 - j : j);
+      const uint32_t rw = __funnelshift_l(w, w, hi ? 32 - j : j);
+      x = (x & keep) | (ry & ~keep);
+      z = (z & keep) | (rw & ~keep);
+    }
+  }
 }
 
 // Histogram sink: shared-memory bins for short lines; longer ones (and any
@@ -260,7 +292,7 @@ __device__ __forceinline__ uint32_t scan2_full(uint32_t x, uint32_t st, ShortCou
   const uint32_t toplen = cl + (uint32_t)(32 - ptop);
   if (fl) first(ctop, toplen); else emit(ctop, toplen);
   const uint32_t S = T ^ (1u << ptop);  // lowest cells of the interior runs
-  if (S) {
+  {  // unconditional: with no interior run every count below is zero
     const uint32_t t1 = T >> 1, t2 = T >> 2, t3 = T >> 3;
     const uint32_t l1 = S & t1;
     const uint32_t l2 = S & t2 & ~t1;
@@ -294,7 +326,7 @@ __device__ __forceinline__ uint32_t scanb_full(uint32_t x, uint32_t st, ShortCou
     emit(f);
   const uint32_t T = (x ^ (x << 1)) & 0xFFFFFFFEu;
   const uint32_t Sb = T & x & lowmask(zt);  // lowest cells of interior black runs
-  if (Sb) {
+  {  // unconditional, as in scan2_full
     const uint32_t t1 = T >> 1, t2 = T >> 2, t3 = T >> 3;
     sc.d12 += __popc(Sb & t1) + (__popc(Sb & t2 & ~t1) << 16);
     sc.d3 += __popc(Sb & t3 & ~(t1 | t2));
@@ -832,6 +864,17 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           const int col0 = jw0 + 32 * c;
           const int j = col0 + lane;
           const uint32_t R = Rw_s[c * 32 + lane];
+          // row words (lane = row) and diagonal words (lane = diagonal: a bit
+          // reverse and a lane rotate of the column words, then a transpose)
+          uint32_t RW = R, D;
+          {
+            const uint32_t rb = __brev(R);
+            D = __funnelshift_r(rb, rb, 31 - lane);
+            if constexpr (!XR)
+              transpose32x2(RW, D, lane);
+            else
+              D = transpose32(D, lane);
+          }
 
           // ---- operator III, upper part of full column j (rows < j); cross:
           // the whole column, whose first run ends at the bottom border
@@ -856,7 +899,6 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
 
           // ---- operator III, lower part of full column irow = upper row irow
           if constexpr (!XR) {
-            const uint32_t RW = transpose32(R, lane);
             const int lo = irow + 1 - col0;  // first valid bit of the row
             if (lo <= 31 && !(rst & ST_DONE) && row_valid) {
               auto emitr = [&](uint32_t col, uint32_t len) { hs.add2(col, len); };
@@ -879,8 +921,6 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
 
           // ---- operator II: diagonal pieces (lane d)
           {
-            const uint32_t rb = __brev(R);
-            const uint32_t D = transpose32(__funnelshift_r(rb, rb, 31 - lane), lane);
             const int k = col0 - r0 + d;  // diagonal of this sub-block's upper segment
             auto emitd = [&](uint32_t len) { hs.add(HIST_DIAG, len); };
             auto firstd = [&](uint32_t len) {
