@@ -711,6 +711,24 @@ void launch_embed(SeriesDesc* d_sd, int count, int64_t max_n_mp, int sms, cudaSt
   if (blocks < 1) blocks = 1;
   embed_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
 }
+// Longest length with a non-zero count in histogram blockIdx.z of series
+// blockIdx.y (0 if the histogram is empty), into counters[CNT_LAST + z]:
+// each block takes a grid-stride share of the bins and one atomic max.
+__global__ void last_bin_kernel(SeriesDesc* sd) {
+  SeriesDesc& S = sd[blockIdx.y];
+  const int64_t hl = S.hl;
+  const unsigned long long* __restrict__ h = S.hist + (int64_t)blockIdx.z * (hl + 1);
+  unsigned long long best = 0;
+  for (int64_t l = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l <= hl;
+       l += (int64_t)gridDim.x * blockDim.x)
+    if (h[l]) best = (unsigned long long)l;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+    best = v > best ? v : best;
+  }
+  if ((threadIdx.x & 31) == 0 && best) atomicMax(&S.counters[CNT_LAST + blockIdx.z], best);
+}
+
 int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cross, bool bands,
                   int sms, cudaStream_t st) {
   int64_t blocks = (max_n + 255) / 256;
@@ -737,7 +755,13 @@ int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cro
       ++launched;
     }
   }
-  return launched;
+  // after every histogram update: the last non-zero bins (the merges above
+  // add the lines that cross strip borders)
+  int64_t lb_blocks = (max_n + 4095) / 4096;  // about 16 bins per thread
+  if (lb_blocks > blocks) lb_blocks = blocks;
+  if (lb_blocks < 1) lb_blocks = 1;
+  last_bin_kernel<<<dim3((unsigned)lb_blocks, count, 3), 256, 0, st>>>(d_sd);
+  return launched + 1;
 }
 void launch_sample(const SeriesDesc* d_sd, const int64_t* ii, const int64_t* jj, int64_t count,
                    uint8_t* out, int f64, cudaStream_t st) {

@@ -915,9 +915,11 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       const uint64_t* h = reinterpret_cast<const uint64_t*>(host_ + h_hist + (p.o_hist - o_hist0));
       const int64_t L1 = p.z.hl + 1;
       r.hist = h;
-      measures_from_histograms_rect(h, h + L1, h + 2 * L1,
-                                    p.z.hl, p.z.n, p.z.n2, in[q].st.l_min, in[q].st.v_min,
-                                    in[q].st.w_min, &r.meas);
+      int64_t last[3];
+      for (int t = 0; t < 3; ++t)
+        last[t] = std::min<int64_t>(static_cast<int64_t>(cnt[CNT_LAST + t]), p.z.hl);
+      measures_from_histograms_last(h, h + L1, h + 2 * L1, last, p.z.n, p.z.n2,
+                                    in[q].st.l_min, in[q].st.v_min, in[q].st.w_min, &r.meas);
     }
     rqa_stats_t& s = r.stats;
     s.n_vec = p.z.n;

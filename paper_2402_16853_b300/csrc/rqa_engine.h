@@ -73,6 +73,12 @@ void measures_from_histograms(const uint64_t* hd, const uint64_t* hv, const uint
 void measures_from_histograms_rect(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
                                    int64_t hl, int64_t rows, int64_t cols, int32_t l_min,
                                    int32_t v_min, int32_t w_min, rqa_measures_t* out);
+// The same, reading histogram t only up to last[t] (every bin above it is
+// zero, as the device recorded); the result is identical.
+void measures_from_histograms_last(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
+                                   const int64_t last[3], int64_t rows, int64_t cols,
+                                   int32_t l_min, int32_t v_min, int32_t w_min,
+                                   rqa_measures_t* out);
 
 class Engine {
  public:

@@ -6,8 +6,6 @@
 // own and the result does not depend on the compiler's choice of FMA.
 #include <cmath>
 #include <cstdint>
-#include <utility>
-#include <vector>
 
 #include "../../include/rqa.h"
 
@@ -15,40 +13,59 @@ namespace rqa {
 
 namespace {
 
-// One pass over a histogram: the sums the measures need for lengths >= lo
-// (and the total over all lengths), the longest such length, and the
-// non-zero entries >= lo in ascending order for the entropy.
+// One pass over a histogram h[1..last]: the sums the measures need for
+// lengths >= lo (and the total over all lengths) and the longest such length.
 struct Scan {
+  const uint64_t* h = nullptr;
+  int64_t last = 0;        // bins above last are zero
+  int64_t lo = 1;          // first length counted (l_min, v_min or w_min, at least 1)
   uint64_t count = 0;      // lines with length >= lo
   uint64_t cells = 0;      // sum of their lengths
   uint64_t cells_all = 0;  // sum of the lengths of all lines
   int64_t longest = 0;     // longest length >= lo (0 if none)
-  std::vector<std::pair<int64_t, uint64_t>> nz;
 };
 
-Scan scan(const uint64_t* h, int64_t n, int64_t lo) {
+Scan scan(const uint64_t* h, int64_t last, int64_t lo) {
   Scan s;
-  const int64_t floor_len = lo < 1 ? 1 : lo;
-  for (int64_t l = 1; l <= n; ++l) {
+  s.h = h;
+  s.last = last;
+  s.lo = lo < 1 ? 1 : lo;
+  for (int64_t l = 1; l <= last; ++l) {
     const uint64_t v = h[l];
     if (!v) continue;
     s.cells_all += static_cast<uint64_t>(l) * v;
-    if (l < floor_len) continue;
+    if (l < s.lo) continue;
     s.count += v;
     s.cells += static_cast<uint64_t>(l) * v;
     s.longest = l;
-    s.nz.emplace_back(l, v);
   }
   return s;
 }
 
-// Shannon entropy (natural log) of the lengths >= lo, terms in ascending l.
+// Shannon entropy (natural log) of the lengths >= lo, terms in ascending l
+// (a second pass over the same bins, so no list of them is kept).  Within
+// one histogram equal counts give the same p = v / total and so the same
+// term; the terms of small counts, which most bins hold, are computed once.
 double entropy(const Scan& s) {
   double acc = 0.0;
   const double total = static_cast<double>(s.count);
-  for (const auto& e : s.nz) {
-    const double p = static_cast<double>(e.second) / total;
-    const double term = p * std::log(p);
+  constexpr uint64_t kMemo = 64;
+  double memo[kMemo];
+  uint64_t have = 0;  // bit v: memo[v] holds the term of count v
+  for (int64_t l = s.lo; l <= s.last; ++l) {
+    const uint64_t v = s.h[l];
+    if (!v) continue;
+    double term;
+    if (v < kMemo && ((have >> v) & 1u)) {
+      term = memo[v];
+    } else {
+      const double p = static_cast<double>(v) / total;
+      term = p * std::log(p);
+      if (v < kMemo) {
+        memo[v] = term;
+        have |= 1ull << v;
+      }
+    }
     acc = acc + term;
   }
   return 0.0 - acc;
@@ -59,6 +76,10 @@ double entropy(const Scan& s) {
 void measures_from_histograms_rect(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
                                    int64_t n, int64_t rows, int64_t cols, int32_t l_min,
                                    int32_t v_min, int32_t w_min, rqa_measures_t* out);
+void measures_from_histograms_last(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
+                                   const int64_t last[3], int64_t rows, int64_t cols,
+                                   int32_t l_min, int32_t v_min, int32_t w_min,
+                                   rqa_measures_t* out);
 
 void measures_from_histograms(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
                               int64_t n, int32_t l_min, int32_t v_min, int32_t w_min,
@@ -69,7 +90,17 @@ void measures_from_histograms(const uint64_t* hd, const uint64_t* hv, const uint
 void measures_from_histograms_rect(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
                                    int64_t n, int64_t rows, int64_t cols, int32_t l_min,
                                    int32_t v_min, int32_t w_min, rqa_measures_t* out) {
-  const Scan d = scan(hd, n, l_min), v = scan(hv, n, v_min), w = scan(hw, n, w_min);
+  const int64_t last[3] = {n, n, n};
+  measures_from_histograms_last(hd, hv, hw, last, rows, cols, l_min, v_min, w_min, out);
+}
+
+void measures_from_histograms_last(const uint64_t* hd, const uint64_t* hv, const uint64_t* hw,
+                                   const int64_t last[3], int64_t rows, int64_t cols,
+                                   int32_t l_min, int32_t v_min, int32_t w_min,
+                                   rqa_measures_t* out) {
+  // bins above last[t] are zero and add nothing to any sum
+  const Scan d = scan(hd, last[0], l_min), v = scan(hv, last[1], v_min),
+             w = scan(hw, last[2], w_min);
   // every recurrence point lies on exactly one vertical line
   const uint64_t rp = v.cells_all;
   out->n_vec = rows;

@@ -84,6 +84,20 @@ class _CStats(ctypes.Structure):
 
 
 MEASURE_FIELDS = list(_MEAS_D + _MEAS_I)
+
+
+def _struct_dtype(cls) -> np.dtype:
+    """The numpy dtype with the field names, types and offsets of a ctypes
+    structure (so an array of it can be passed where the C ABI wants one)."""
+    kinds = {ctypes.c_int32: np.int32, ctypes.c_int64: np.int64, ctypes.c_double: np.float64}
+    return np.dtype({"names": [f for f, _ in cls._fields_],
+                     "formats": [kinds[t] for _, t in cls._fields_],
+                     "offsets": [getattr(cls, f).offset for f, _ in cls._fields_],
+                     "itemsize": ctypes.sizeof(cls)})
+
+
+_SETTINGS_DT = _struct_dtype(_CSettings)
+_MEASURES_DT = _struct_dtype(_CMeasures)
 _lib = None
 
 
@@ -348,17 +362,29 @@ class Batch:
     def run(self, settings: Sequence[Settings], series: Sequence[np.ndarray]):
         """Returns (list of measure dicts or None, list of statuses, rc)."""
         k = len(series)
+        if len(settings) != k:
+            raise ValueError("one Settings per series")
         arrs = [_f64(s) for s in series]
-        cs = (_CSettings * k)(*[_cs(s) for s in settings])
-        ptrs = (ctypes.POINTER(ctypes.c_double) * k)(
-            *[a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs])
-        lens = (ctypes.c_int64 * k)(*[len(a) for a in arrs])
-        out = (_CMeasures * k)()
-        st = (ctypes.c_int32 * k)()
-        rc = load().rqa_batch_run(self._h, cs, ptrs, lens, k, out, st)
+        # numpy arrays in the C layouts: one vectorised fill per field
+        # instead of a ctypes object per series
+        cs = np.zeros(k, _SETTINGS_DT)
+        for f in _SETTINGS_DT.names:
+            cs[f] = [getattr(s, f) for s in settings]
+        ptrs = np.fromiter((a.__array_interface__["data"][0] for a in arrs), np.uintp, k)
+        lens = np.fromiter((a.shape[0] for a in arrs), np.int64, k)
+        out = np.zeros(k, _MEASURES_DT)
+        st = np.zeros(k, np.int32)
+        P = ctypes.POINTER
+        rc = load().rqa_batch_run(self._h, cs.ctypes.data_as(P(_CSettings)),
+                                  ptrs.ctypes.data_as(P(P(ctypes.c_double))),
+                                  lens.ctypes.data_as(P(ctypes.c_int64)), k,
+                                  out.ctypes.data_as(P(_CMeasures)),
+                                  st.ctypes.data_as(P(ctypes.c_int32)))
         self._arrs = arrs
-        res = [(_meas(out[q]) if st[q] == 0 else None) for q in range(k)]
-        return res, [int(x) for x in st], int(rc)
+        sts = st.tolist()
+        res = [dict(zip(MEASURE_FIELDS, row)) if q == 0 else None
+               for row, q in zip(out.tolist(), sts)]
+        return res, sts, int(rc)
 
     def histogram(self, q: int, kind: int) -> np.ndarray:
         ln = ctypes.c_int64()
