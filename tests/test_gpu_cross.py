@@ -91,6 +91,18 @@ def test_exact_ties(norm):
     assert st["rechecks"] > 0
 
 
+@pytest.mark.parametrize("norm", [0, 1, 2])
+def test_long_lines_end_together(norm):
+    """Constant series with one outlier each: the white row and column end
+    thousands of runs longer than the shared bins in the same sub-blocks."""
+    x = synth.constant(4100, 0.3)
+    y = synth.constant(3900, 0.3)
+    x[1500] = 100.0
+    y[2600] = -100.0
+    _, _, want = check_cross(x, y, m=2, tau=1, eps=0.01, norm=norm, theiler=0)
+    assert want["hd"][1024:].sum() > 1000 and want["hv"][1024:].sum() > 1000
+
+
 @pytest.mark.parametrize("p,off", [(3, 0), (5, 2)])
 def test_periodic(p, off):
     x = synth.periodic(1200, p)

@@ -80,6 +80,19 @@ def test_constant_series(norm, w):
     check_parity(s, m=2, tau=2, eps=0.01, norm=norm, theiler=w)
 
 
+@pytest.mark.parametrize("norm", [0, 1, 2])
+@pytest.mark.parametrize("w", [0, 1])
+def test_long_lines_end_together(norm, w):
+    """A constant series with one outlier: the outlier's white row and column
+    end thousands of long column, row and diagonal runs in the same
+    sub-blocks, every lane of a warp at once, so lengths beyond the shared
+    bins pile up between two drains of the per-warp queue."""
+    s = synth.constant(4100, 0.3)
+    s[1500] = 100.0
+    _, _, want = check_parity(s, m=2, tau=1, eps=0.01, norm=norm, theiler=w)
+    assert want["hd"][1024:].sum() > 1000 and want["hv"][1024:].sum() > 1000
+
+
 @pytest.mark.parametrize("p", [2, 3, 37])
 def test_periodic(p):
     s = synth.periodic(1300, p, offset=2)
