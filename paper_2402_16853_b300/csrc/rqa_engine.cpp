@@ -41,8 +41,9 @@ void parallel_for(int count, int per_thread, F&& f) {
 }
 
 // RQA_TRACE=1: one line per run on stderr with the host phases of the run
-// (plan, staging, enqueue, wait for the device, results) and the device
-// times, for finding where a call spends its time.
+// (plan, staging, enqueue, the device run with the measures computed as each
+// stream group's results land, the finish) and the device times, for finding
+// where a call spends its time.
 bool trace_enabled() {
   static const bool on = [] {
     const char* e = std::getenv("RQA_TRACE");
@@ -344,6 +345,8 @@ Engine::Engine(int device) : dev_(device) {
   for (auto& a : aux_) cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking);
   cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming);
   for (auto& j : join_) cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+  for (auto& t : tiled_) cudaEventCreate(&t);
+  for (auto& d : done_) cudaEventCreateWithFlags(&d, cudaEventDisableTiming);
 }
 
 Engine::~Engine() {
@@ -353,6 +356,10 @@ Engine::~Engine() {
     if (e) cudaEventDestroy(e);
   for (auto& j : join_)
     if (j) cudaEventDestroy(j);
+  for (auto& t : tiled_)
+    if (t) cudaEventDestroy(t);
+  for (auto& d : done_)
+    if (d) cudaEventDestroy(d);
   if (fork_) cudaEventDestroy(fork_);
   for (auto& a : aux_)
     if (a) cudaStreamDestroy(a);
@@ -453,8 +460,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   using Key = std::tuple<int, int, int, int, int>;  // m, norm, f64, warps, cross
   std::map<Key, int> cls_of;
   std::vector<Key> classes;
-  int64_t max_n = 0, max_n_mp = 0, total_items = 0;
-  bool any_fp32 = false, any_sym = false, any_cross = false, any_bands = false;
+  int64_t max_n_mp = 0, total_items = 0;
+  bool any_fp32 = false;
   for (int q = 0; q < count; ++q) {
     std::string msg;
     const int s = validate_input(in[q], &msg);
@@ -505,7 +512,6 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       p.z = sizes_for(in[q].st, in[q].N, in[q].dev == nullptr, in[q].cross, in[q].N2,
                       in[q].dev2 == nullptr, false, warps, bands_ok);
     dev_idx[q] = nrun++;
-    (p.z.cross ? any_cross : any_sym) = true;
     // kernel class: (m, norm, f64, warps, kind), kind 0 RQA, 1 cross, 2 matrix,
     // plus 3 for the row-band instantiation of each
     const int bk = p.z.nbands > 1 ? 3 : 0;
@@ -518,19 +524,60 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       classes.push_back(k);
     }
     p.cls = it->second;
-    max_n = std::max(max_n, p.z.cross ? p.z.n + p.z.n2 : p.z.n);
     if (!p.z.f64 && !p.z.matrix) {
       any_fp32 = true;
       max_n_mp = std::max(max_n_mp, (p.z.n + (p.z.cross ? p.z.n2 : 0)) * p.z.mp);
     }
     total_items += p.z.nitems;
-    any_bands = any_bands || p.z.nbands > 1;
   }
   const int ncls = static_cast<int>(classes.size());
   if (ncls == 0) {  // nothing runnable: report the first validation failure
     for (const auto& r : results)
       if (r.status != RQA_OK) return r.status;
     return RQA_OK;
+  }
+
+  // Classes run on up to kAux side streams so that small classes overlap
+  // (their CTAs never wait on each other); the longest work goes first, each
+  // class to the least loaded stream.  A single class runs on the main stream.
+  std::vector<int> cls_order, cls_stream;
+  const int nside = ncls > 1 ? std::min(ncls, kAux) : 0;
+  std::vector<double> cls_work(ncls, 0.0);
+  for (int q = 0; q < count; ++q)
+    if (plan[q].run)
+      cls_work[plan[q].cls] +=
+          static_cast<double>(plan[q].z.n) * static_cast<double>(plan[q].z.n2);
+  assign_streams(cls_work, nside, cls_order, cls_stream);
+  // The series of each stream form a group (one group on the main stream
+  // when nothing runs beside it) with contiguous descriptors, histograms and
+  // counters: the group's merges and read-back follow its own tile kernels
+  // on its stream, and the host computes its measures while the other groups
+  // still run.
+  const int ngrp = nside ? nside : 1;
+  auto grp_of = [&](int q) { return nside ? cls_stream[plan[q].cls] : 0; };
+  struct Grp {
+    int first = 0, count = 0;
+    int64_t max_n = 0;
+    bool sym = false, cross = false, bands = false;
+    double work = 0.0;
+    size_t o_rb = 0, rb_bytes = 0;  // [histograms][counters] of the group
+  };
+  std::vector<Grp> grp(ngrp);
+  std::vector<int> order;  // runnable series, group by group
+  order.reserve(nrun);
+  for (int g = 0; g < ngrp; ++g) {
+    grp[g].first = static_cast<int>(order.size());
+    for (int q = 0; q < count; ++q) {
+      if (!plan[q].run || grp_of(q) != g) continue;
+      const Sizes& z = plan[q].z;
+      dev_idx[q] = static_cast<int>(order.size());
+      order.push_back(q);
+      grp[g].max_n = std::max(grp[g].max_n, z.cross ? z.n + z.n2 : z.n);
+      (z.cross ? grp[g].cross : grp[g].sym) = true;
+      grp[g].bands = grp[g].bands || z.nbands > 1;
+      grp[g].work += static_cast<double>(z.n) * static_cast<double>(z.n2);
+    }
+    grp[g].count = static_cast<int>(order.size()) - grp[g].first;
   }
 
   // ---- arena layout: [descs][items][queues | hists | counters | ends | boundary
@@ -549,20 +596,24 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   const size_t o_zero = off;
   const size_t o_queue = off;
   off += align256(sizeof(int) * ncls);
-  const size_t o_hist0 = off;
-  for (auto& p : plan)
-    if (p.run) {
+  const size_t o_hist0 = off;  // per group: [histograms][counters]
+  size_t hist_bytes = 0, cnt_bytes = 0;
+  for (Grp& gr : grp) {
+    gr.o_rb = off;
+    for (int i = gr.first; i < gr.first + gr.count; ++i) {
+      P& p = plan[order[i]];
       p.o_hist = off;
       off += p.z.hist;
+      hist_bytes += p.z.hist;
     }
-  const size_t hist_bytes = off - o_hist0;
-  const size_t o_cnt0 = off;
-  for (auto& p : plan)
-    if (p.run) {
+    for (int i = gr.first; i < gr.first + gr.count; ++i) {
+      P& p = plan[order[i]];
       p.o_cnt = off;
       off += p.z.cnt;
+      cnt_bytes += p.z.cnt;
     }
-  const size_t cnt_bytes = off - o_cnt0;
+    gr.rb_bytes = off - gr.o_rb;
+  }
   for (auto& p : plan)
     if (p.run) {
       p.o_ends = off;
@@ -592,15 +643,14 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   const size_t arena_bytes = off;
 
   // host staging: [descs][items][band tables] (the arena's first o_zero bytes,
-  // copied in one piece) [hist readback][counter readback][series]
+  // copied in one piece) [histogram and counter read-back, laid out as on the
+  // device from o_hist0][series]
   size_t hoff = 0;
   const size_t h_sd = hoff;
   const size_t h_items = o_items - o_sd;
   hoff += o_zero - o_sd;
   const size_t h_hist = hoff;
-  hoff += hist_bytes;
-  const size_t h_cnt = hoff;
-  hoff += cnt_bytes;
+  hoff += hist_bytes + cnt_bytes;
   const size_t h_series = hoff;
   hoff += series_bytes;
 
@@ -760,18 +810,6 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   }
   const bool replay = use_graph && graph_ && key == graph_key_;
 
-  // Classes run on up to kAux side streams so that small classes overlap
-  // (their CTAs never wait on each other); the longest work goes first, each
-  // class to the least loaded stream.  One class runs on the main stream.
-  std::vector<int> cls_order, cls_stream;
-  const int nside = ncls > 1 ? std::min(ncls, kAux) : 0;
-  {
-    std::vector<double> work(ncls, 0.0);
-    for (int q = 0; q < count; ++q)
-      if (plan[q].run)
-        work[plan[q].cls] += static_cast<double>(plan[q].z.n) * static_cast<double>(plan[q].z.n2);
-    assign_streams(work, nside, cls_order, cls_stream);
-  }
   // timing events are external nodes when captured, so replays record them
   const unsigned evflags = use_graph ? cudaEventRecordExternal : cudaEventRecordDefault;
 
@@ -798,6 +836,11 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       launch_embed(d_sd, nrun, max_n_mp, sms_, st);
       ++launches;
     }
+    // the series state prepare wrote (error band and bound), read back before
+    // the fork so that every group's completion implies it
+    if ((e = cudaMemcpyAsync(host_ + h_sd, arena_ + o_sd, sizeof(SeriesDesc) * nrun,
+                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync(series state)");
     if ((e = cudaEventRecordWithFlags(ev_[1], st, evflags)) != cudaSuccess)
       return cuda_fail(e, "cudaEventRecord");
     if (nside) {
@@ -838,22 +881,30 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       ++launches;
       ctas_total += grid;
     }
+    // per group, on its own stream after its tile kernels: the merges, then
+    // one read-back of the group's histograms and counters
+    for (int g = 0; g < ngrp; ++g) {
+      cudaStream_t gs = nside ? aux_[g] : st;
+      const Grp& gr = grp[g];
+      if ((e = cudaEventRecordWithFlags(nside ? tiled_[g] : ev_[2], gs, evflags)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventRecord");
+      if (gr.count > 0) {
+        launches += launch_merges(d_sd + gr.first, gr.count, gr.max_n, gr.sym, gr.cross,
+                                  gr.bands, sms_, gs);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "merge kernels launch");
+        if ((e = cudaMemcpyAsync(host_ + h_hist + (gr.o_rb - o_hist0), arena_ + gr.o_rb,
+                                 gr.rb_bytes, cudaMemcpyDeviceToHost, gs)) != cudaSuccess)
+          return cuda_fail(e, "cudaMemcpyAsync(histograms)");
+      }
+      if ((e = cudaEventRecordWithFlags(done_[g], gs, evflags)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventRecord");
+    }
     for (int k = 0; k < nside; ++k) {
       if ((e = cudaEventRecord(join_[k], aux_[k])) != cudaSuccess)
         return cuda_fail(e, "cudaEventRecord");
       if ((e = cudaStreamWaitEvent(st, join_[k], 0)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamWaitEvent");
     }
-    if ((e = cudaEventRecordWithFlags(ev_[2], st, evflags)) != cudaSuccess)
-      return cuda_fail(e, "cudaEventRecord");
-    launches += launch_merges(d_sd, nrun, max_n, any_sym, any_cross, any_bands, sms_, st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "merge kernels launch");
-    if ((e = cudaMemcpyAsync(host_ + h_hist, arena_ + o_hist0, hist_bytes + cnt_bytes,
-                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-      return cuda_fail(e, "cudaMemcpyAsync(histograms)");
-    if ((e = cudaMemcpyAsync(host_ + h_sd, arena_ + o_sd, sizeof(SeriesDesc) * nrun,
-                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-      return cuda_fail(e, "cudaMemcpyAsync(series state)");
     if ((e = cudaEventRecordWithFlags(ev_[3], st, evflags)) != cudaSuccess)
       return cuda_fail(e, "cudaEventRecord");
     return RQA_OK;
@@ -890,22 +941,31 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     if (rc != RQA_OK) return rc;
   }
   tp[3] = clk::now();
-  ce = cudaStreamSynchronize(st);
-  tp[4] = clk::now();
-  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
-  cudaEventElapsedTime(&tile_ms_, ev_[1], ev_[2]);
-  cudaEventElapsedTime(&total_ms_, ev_[0], ev_[3]);
-  last_sd_ = d_sd;
-  last_f64_ = plan[0].run && plan[0].z.f64;
-  last_matrix_ = plan[0].run && plan[0].z.matrix;
-  last_stream_ = st;
-
-  // ---- results (per series in parallel: histogram copy and host measures)
-  parallel_for(count, 8, [&](int q) {
+  // ---- results: the measures of each series as soon as its group's
+  // read-back has landed, the groups in the order their streams should finish
+  std::vector<int> grp_order(ngrp);
+  for (int g = 0; g < ngrp; ++g) grp_order[g] = g;
+  std::stable_sort(grp_order.begin(), grp_order.end(),
+                   [&](int a, int b) { return grp[a].work < grp[b].work; });
+  std::vector<int> work_list;
+  work_list.reserve(nrun);
+  for (int g : grp_order)
+    for (int i = grp[g].first; i < grp[g].first + grp[g].count; ++i) work_list.push_back(order[i]);
+  std::atomic<bool> wait_failed{false};
+  parallel_for(nrun, 8, [&](int i) {
+    const int q = work_list[i];
     const P& p = plan[q];
     SeriesResult& r = results[q];
-    if (!p.run) return;
-    const uint64_t* cnt = reinterpret_cast<const uint64_t*>(host_ + h_cnt + (p.o_cnt - o_cnt0));
+    thread_local int current_dev = -1;  // a worker thread waits on this device's events
+    if (current_dev != dev_) {
+      cudaSetDevice(dev_);
+      current_dev = dev_;
+    }
+    if (cudaEventSynchronize(done_[grp_of(q)]) != cudaSuccess) {
+      wait_failed = true;
+      return;
+    }
+    const uint64_t* cnt = reinterpret_cast<const uint64_t*>(host_ + h_hist + (p.o_cnt - o_hist0));
     const SeriesDesc& d = hsd[dev_idx[q]];
     r.n = p.z.n;
     r.n2 = p.z.n2;
@@ -936,13 +996,34 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     s.band_rows = p.z.nbands > 1 ? p.z.band_h : 0;
     s.warps_per_cta = p.z.tc.warps;
     s.cols_per_lane = p.z.tc.cols;
-    s.kernel_ms = tile_ms_;
-    s.total_ms = total_ms_;
     s.h2d_bytes = static_cast<int64_t>((o_zero - o_sd) + series_bytes);
     s.d2h_bytes = static_cast<int64_t>(hist_bytes + cnt_bytes + sizeof(SeriesDesc) * nrun);
     s.launches = launches;
     s.ctas = static_cast<int32_t>(ctas_total);
   });
+  ce = cudaStreamSynchronize(st);
+  tp[4] = clk::now();
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
+  if (wait_failed) return fail(RQA_ECUDA, "waiting for a group's read-back failed");
+  if (nside) {  // tiles: from the fork to the last group's tile kernels
+    tile_ms_ = 0.f;
+    for (int g = 0; g < ngrp; ++g) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev_[1], tiled_[g]);
+      tile_ms_ = std::max(tile_ms_, ms);
+    }
+  } else {
+    cudaEventElapsedTime(&tile_ms_, ev_[1], ev_[2]);
+  }
+  cudaEventElapsedTime(&total_ms_, ev_[0], ev_[3]);
+  for (int q : order) {
+    results[q].stats.kernel_ms = tile_ms_;
+    results[q].stats.total_ms = total_ms_;
+  }
+  last_sd_ = d_sd;
+  last_f64_ = plan[0].run && plan[0].z.f64;
+  last_matrix_ = plan[0].run && plan[0].z.matrix;
+  last_stream_ = st;
   int first_err = RQA_OK;
   for (int q = 0; q < count && first_err == RQA_OK; ++q) {
     const SeriesResult& r = results[q];
@@ -960,7 +1041,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     };
     std::fprintf(stderr,
                  "rqa trace: series=%d classes=%d plan=%.3f staging=%.3f enqueue=%.3f "
-                 "wait=%.3f results=%.3f ms; device total=%.3f tile=%.3f ms%s\n",
+                 "device+results=%.3f finish=%.3f ms; device total=%.3f tile=%.3f ms%s\n",
                  count, ncls, ms(0, 1), ms(1, 2), ms(2, 3), ms(3, 4), ms(4, 5), total_ms_,
                  tile_ms_, use_graph ? (replay ? " (graph replay)" : " (graph capture)") : "");
   }

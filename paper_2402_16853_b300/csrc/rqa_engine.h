@@ -123,6 +123,10 @@ class Engine {
   cudaStream_t aux_[kAux] = {};
   cudaEvent_t fork_ = nullptr;
   cudaEvent_t join_[kAux] = {};
+  // per stream group: its tile kernels are done (timing) / its histograms
+  // and counters have landed in the pinned staging (waited on by the host)
+  cudaEvent_t tiled_[kAux] = {};
+  cudaEvent_t done_[kAux] = {};
   std::string err_;
   float tile_ms_ = 0.f, total_ms_ = 0.f;
   // last run, for sample()
