@@ -677,17 +677,31 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
         const int r0 = b << 5;
         if constexpr (!MX) {  // row vectors of rows r0 .. r0+31 into this warp's buffer
           const int i = r0 + lane;
+          if constexpr (!F64) {
+            // 16-byte loads of the padded FP32 vector (mp is a multiple of 4)
+            // and 16-byte stores; the L2 layout holds each coordinate twice.
+            // Slots past the m coordinates are never read.
+            const float4* src = reinterpret_cast<const float4*>(xe + (int64_t)i * mp);
+            float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(rowbuf) + lane * RE);
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (NORM == 1) {
 #pragma unroll
-          for (int k = 0; k < RE; ++k) {
-            T v = (T)0;
-            if constexpr (F64) {
-              if (i < n && k < M) v = sser[i + k * tau];
-            } else if constexpr (NORM == 1) {
-              if (i < n && (k >> 1) < M) v = xe[(int64_t)i * mp + (k >> 1)];
+              for (int p = 0; p < (RE / 4 + 1) / 2; ++p) {
+                const float4 v = i < n ? src[p] : z4;
+                dst[2 * p] = make_float4(v.x, v.x, v.y, v.y);
+                if (2 * p + 1 < RE / 4) dst[2 * p + 1] = make_float4(v.z, v.z, v.w, v.w);
+              }
             } else {
-              if (i < n && k < M) v = xe[(int64_t)i * mp + k];
+#pragma unroll
+              for (int p = 0; p < RE / 4; ++p) dst[p] = i < n ? src[p] : z4;
             }
-            rowbuf[lane * RE + k] = v;
+          } else {
+#pragma unroll
+            for (int k = 0; k < RE; ++k) {
+              T v = (T)0;
+              if (i < n && k < M) v = sser[i + k * tau];
+              rowbuf[lane * RE + k] = v;
+            }
           }
         }
         __syncwarp();
