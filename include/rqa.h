@@ -309,6 +309,16 @@ int rqa_selftest_bounded_wait(int32_t* status, int64_t* cycles_waited);
  * roofline's per-pair operation count; the benchmark divides by the larger of
  * this and SMs x 128 lanes x clock.  Takes a few milliseconds. */
 int rqa_probe_alu(int32_t kind, double* ops_per_s);
+/* ------------------------------------------------------------ preloading
+ * The paper has no counterpart.  CUDA loads kernels lazily, at their first
+ * launch, and a load can stall the whole context while other work runs.
+ * rqa_preload_kernels() loads every kernel a run can launch (all tile kernel
+ * instantiations and the preparation and merge kernels) into the current
+ * device's context, once per process; later calls return at once.
+ * *loaded (may be NULL) receives the number of kernels it loaded.
+ * rqa_server_create calls it.  RQA_ENODEV without an sm_103 device,
+ * RQA_ECUDA if a load fails. */
+int rqa_preload_kernels(int32_t* loaded);
 /* ----------------------------------------------------------------- batched
  * Many independent series in one submission: the work of all series is one
  * queue of (series, strip) items processed by persistent CTAs, one launch

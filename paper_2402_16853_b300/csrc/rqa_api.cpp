@@ -5,6 +5,7 @@
 
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -231,6 +232,36 @@ int rqa_batch_create(rqa_batch** out) {
     return RQA_ENOMEM;
   }
   *out = b;
+  return RQA_OK;
+}
+
+int rqa_preload_kernels(int32_t* loaded) {
+  std::string msg;
+  int dev = 0;
+  const int rc = find_device(&dev, &msg);
+  if (rc != RQA_OK) return rc;
+  // once per device and process; the lock also keeps two first callers from
+  // loading at the same time
+  static std::mutex mu;
+  static uint64_t done = 0;  // bit d: device d preloaded
+  static int32_t count[64] = {};
+  std::lock_guard<std::mutex> lk(mu);
+  const uint64_t bit = dev < 64 ? (1ull << dev) : 0;
+  if (!(done & bit)) {
+    const int t = rqa::preload_tile_kernels();
+    const int a = t < 0 ? -1 : rqa::preload_aux_kernels();
+    if (t < 0 || a < 0) {
+      cudaGetLastError();
+      return RQA_ECUDA;
+    }
+    if (bit) {
+      done |= bit;
+      count[dev] = t + a;
+    }
+    if (loaded) *loaded = t + a;
+    return RQA_OK;
+  }
+  if (loaded) *loaded = count[dev];
   return RQA_OK;
 }
 

@@ -729,6 +729,25 @@ __global__ void last_bin_kernel(SeriesDesc* sd) {
   if ((threadIdx.x & 31) == 0 && best) atomicMax(&S.counters[CNT_LAST + blockIdx.z], best);
 }
 
+int preload_aux_kernels() {
+  const void* fns[] = {
+      reinterpret_cast<const void*>(prepare_kernel),
+      reinterpret_cast<const void*>(embed_kernel),
+      reinterpret_cast<const void*>(merge_rows_kernel),
+      reinterpret_cast<const void*>(merge_diags_kernel),
+      reinterpret_cast<const void*>(merge_cols_kernel),
+      reinterpret_cast<const void*>(merge_cross_diags_kernel),
+      reinterpret_cast<const void*>(merge_cross_cols_kernel),
+      reinterpret_cast<const void*>(join_loi_kernel),
+      reinterpret_cast<const void*>(diag_full_kernel),
+      reinterpret_cast<const void*>(last_bin_kernel),
+  };
+  cudaFuncAttributes a;
+  for (const void* f : fns)
+    if (cudaFuncGetAttributes(&a, f) != cudaSuccess) return -1;
+  return static_cast<int>(sizeof(fns) / sizeof(fns[0]));
+}
+
 int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cross, bool bands,
                   int sms, cudaStream_t st) {
   int64_t blocks = (max_n + 255) / 256;

@@ -347,6 +347,14 @@ Engine::Engine(int device) : dev_(device) {
   for (auto& j : join_) cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
   for (auto& t : tiled_) cudaEventCreate(&t);
   for (auto& d : done_) cudaEventCreateWithFlags(&d, cudaEventDisableTiming);
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev_;
+  if (cudaMemPoolCreate(&pool_, &props) != cudaSuccess) {  // plain cudaMalloc then
+    cudaGetLastError();
+    pool_ = nullptr;
+  }
 }
 
 Engine::~Engine() {
@@ -361,10 +369,12 @@ Engine::~Engine() {
   for (auto& d : done_)
     if (d) cudaEventDestroy(d);
   if (fork_) cudaEventDestroy(fork_);
+  free_arena(own_);  // every run ended with its stream idle
+  cudaStreamSynchronize(own_);
+  if (pool_) cudaMemPoolDestroy(pool_);
   for (auto& a : aux_)
     if (a) cudaStreamDestroy(a);
   if (own_) cudaStreamDestroy(own_);
-  if (arena_) cudaFree(arena_);
   if (host_) cudaFreeHost(host_);
 }
 
@@ -378,25 +388,35 @@ int Engine::cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? RQA_ENOMEM : RQA_ECUDA;
 }
 
-int Engine::ensure_arena(size_t bytes) {
+void Engine::free_arena(cudaStream_t st) {
+  if (!arena_) return;
+  if (pool_)
+    cudaFreeAsync(arena_, st);
+  else
+    cudaFree(arena_);
+  arena_ = nullptr;
+  arena_cap_ = 0;
+}
+
+// Grow the arena to at least `bytes` (by half again, so growth stays rare).
+// From the pool, the old block is released and the new one taken in the
+// order of `st`, which every previous run of this engine has completed on.
+int Engine::ensure_arena(size_t bytes, cudaStream_t st) {
   if (bytes <= arena_cap_) return RQA_OK;
   if (graph_) {
     cudaGraphExecDestroy(graph_);
     graph_ = nullptr;
     graph_key_.clear();
   }
-  if (arena_) {
-    cudaFree(arena_);
-    arena_ = nullptr;
-    arena_cap_ = 0;
-  }
-  const size_t cap = bytes + bytes / 8;
-  cudaError_t e = cudaMalloc(&arena_, cap);
+  free_arena(st);
+  const size_t cap = bytes + bytes / 2;
+  void* p = nullptr;
+  cudaError_t e = pool_ ? cudaMallocFromPoolAsync(&p, cap, pool_, st) : cudaMalloc(&p, cap);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    arena_ = nullptr;
-    return cuda_fail(e, "cudaMalloc(device arena)");
+    return cuda_fail(e, "device arena allocation");
   }
+  arena_ = static_cast<unsigned char*>(p);
   arena_cap_ = cap;
   return RQA_OK;
 }
@@ -413,7 +433,7 @@ int Engine::ensure_host(size_t bytes) {
     host_ = nullptr;
     host_cap_ = 0;
   }
-  const size_t cap = bytes + bytes / 8;
+  const size_t cap = bytes + bytes / 2;
   cudaError_t e = cudaMallocHost(&host_, cap);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -427,9 +447,15 @@ int Engine::ensure_host(size_t bytes) {
 int Engine::run(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& results,
                 cudaStream_t stream, bool use_graph) {
   const int rc = run_impl(in, results, stream, use_graph);
-  if (rc != RQA_OK)  // a failure of the whole set marks every unfinished series
+  if (rc != RQA_OK) {
+    // a failure of the whole set marks every unfinished series
     for (auto& r : results)
       if (r.status == RQA_OK && !r.hist) r.status = rc;
+    // nothing of this run may still use the arena when the next one grows it
+    cudaStreamSynchronize(stream ? stream : own_);
+    for (auto& a : aux_) cudaStreamSynchronize(a);
+    cudaGetLastError();
+  }
   return rc;
 }
 
@@ -654,7 +680,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   const size_t h_series = hoff;
   hoff += series_bytes;
 
-  int rc = ensure_arena(arena_bytes);
+  int rc = ensure_arena(arena_bytes, st);
   if (rc != RQA_OK) return rc;
   rc = ensure_host(hoff);
   if (rc != RQA_OK) return rc;

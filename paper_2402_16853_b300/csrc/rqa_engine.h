@@ -106,8 +106,9 @@ class Engine {
  private:
   int run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& results,
                cudaStream_t stream, bool use_graph);
-  int ensure_arena(size_t bytes);
+  int ensure_arena(size_t bytes, cudaStream_t st);
   int ensure_host(size_t bytes);
+  void free_arena(cudaStream_t st);
   int fail(int code, const std::string& msg);
   int cuda_fail(cudaError_t e, const char* what);
 
@@ -115,6 +116,9 @@ class Engine {
   cudaStream_t own_ = nullptr;
   unsigned char* arena_ = nullptr;
   size_t arena_cap_ = 0;
+  // the arena comes from this engine's own stream-ordered pool, so growing
+  // it does not synchronise the device (other engines' work keeps running)
+  cudaMemPool_t pool_ = nullptr;
   unsigned char* host_ = nullptr;  // pinned staging
   size_t host_cap_ = 0;
   cudaEvent_t ev_[4] = {nullptr, nullptr, nullptr, nullptr};

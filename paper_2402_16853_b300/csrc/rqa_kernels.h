@@ -38,6 +38,10 @@ void launch_plot(const SeriesDesc* d_sd, int64_t i0, int64_t j0, int64_t rows, i
                  uint32_t* out, int f64, int m, int norm, int sms, cudaStream_t st);
 // Bounded-wait self-test (status[3] in device memory: status, cycles, abort).
 void launch_wait_selftest(unsigned long long* status, cudaStream_t st);
+// Load every kernel of the library into the current context (see
+// rqa_preload_kernels); the count loaded, or -1 on a CUDA error.
+int preload_tile_kernels();
+int preload_aux_kernels();
 void launch_sample(const SeriesDesc* d_sd, const int64_t* ii, const int64_t* jj, int64_t count,
                    uint8_t* out, int f64, cudaStream_t st);
 

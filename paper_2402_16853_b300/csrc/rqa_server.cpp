@@ -142,6 +142,10 @@ int rqa_server_create(size_t mem_budget_bytes, int32_t max_slots, rqa_server** o
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
   if (major != 10 || minor != 3) return RQA_ENODEV;
+  // every kernel loaded before the first request: a lazy load in the middle
+  // of other requests' work stalls them all
+  const int pre = rqa_preload_kernels(nullptr);
+  if (pre != RQA_OK) return pre;
   rqa_server* s = new (std::nothrow) rqa_server();
   if (!s) return RQA_ENOMEM;
   s->budget = mem_budget_bytes;

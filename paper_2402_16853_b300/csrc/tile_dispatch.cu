@@ -1,4 +1,5 @@
 // tile_dispatch.cu -- selects the tile kernel instantiation for a series.
+#include "../../include/rqa.h"
 #include "rqa_kernels.h"
 #include "rqa_tile.cuh"
 
@@ -11,6 +12,32 @@ TileFn tile_kernel_for(int m, int norm, int cols, bool f64, bool cross, bool ban
     case 2: return cross ? tile_kernel_cross_norm2(m, cols, f64, bands) : tile_kernel_norm2(m, cols, f64, bands);
     default: return nullptr;
   }
+}
+
+// Load every tile kernel instantiation now: with lazy module loading a
+// kernel is otherwise loaded at its first launch, which can stall the whole
+// context in the middle of other work.  Querying a function's attributes
+// loads it.
+int preload_tile_kernels() {
+  int loaded = 0;
+  cudaFuncAttributes a;
+  for (int bands = 0; bands < 2; ++bands) {
+    for (int cross = 0; cross < 2; ++cross)
+      for (int f64 = 0; f64 < 2; ++f64)
+        for (int norm = 0; norm < 3; ++norm)
+          for (int m = 1; m <= RQA_MAX_M; ++m) {
+            TileFn fn = tile_kernel_for(m, norm, 4, f64 != 0, cross != 0, bands != 0);
+            if (!fn) continue;
+            if (cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(fn)) != cudaSuccess)
+              return -1;
+            ++loaded;
+          }
+    if (TileFn fn = tile_kernel_matrix(4, bands != 0)) {
+      if (cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(fn)) != cudaSuccess) return -1;
+      ++loaded;
+    }
+  }
+  return loaded;
 }
 
 size_t tile_smem_for(int m, int norm, bool f64, int warps, int cols) {

@@ -154,6 +154,7 @@ def load(path: str = LIB_PATH):
         "rqa_autotune_clear": (None, []),
         "rqa_selftest_bounded_wait": (c.c_int, [P(c.c_int32), P(c.c_int64)]),
         "rqa_probe_alu": (c.c_int, [c.c_int32, P(c.c_double)]),
+        "rqa_preload_kernels": (c.c_int, [P(c.c_int32)]),
         "rqa_autotune_last_error": (c.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -552,6 +553,17 @@ def probe_alu() -> dict:
             raise RQAError(rc, "rqa_probe_alu")
         res[name] = v.value
     return res
+
+
+def preload_kernels() -> int:
+    """Load every kernel of the library into the current device's context
+    now (once per process) instead of at first launch; returns how many.
+    Servers call it at creation; a latency-sensitive caller can too."""
+    n = ctypes.c_int32()
+    rc = load().rqa_preload_kernels(ctypes.byref(n))
+    if rc:
+        raise RQAError(rc, "rqa_preload_kernels")
+    return int(n.value)
 
 
 def autotune_clear() -> None:

@@ -200,3 +200,21 @@ def test_served_banded_requests_equal_alone():
             assert_same_measures(m, a)
     finally:
         srv.close()
+
+
+def test_preload_kernels_once_per_process():
+    """Every tile kernel instantiation (m = 1..10, three norms, FP32 and FP64,
+    RQA and cross, with and without row bands, and the two matrix-input
+    ones) plus the ten preparation and merge kernels are loaded; a second
+    call finds them loaded and reports the same count."""
+    n = gp.preload_kernels()
+    assert n == 10 * 3 * 2 * 2 * 2 + 2 + 10
+    assert gp.preload_kernels() == n
+    # a run afterwards is unaffected
+    s = synth.ar1(600, 5, 0.9)
+    st = gp.Settings(m=2, tau=1, eps=0.5, norm=1, theiler=1)
+    want = oracle.rqa(s, oracle.Settings(m=2, tau=1, eps=0.5, norm=1, theiler=1))
+    r = gp.RQA(st)
+    r.run(s)
+    hd, hv, hw = r.histograms()
+    assert np.array_equal(hd, want["hd"]) and np.array_equal(hw, want["hw"])
