@@ -412,6 +412,11 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
   asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
   return r;
 }
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
 
 // Exact FP64 decision, in the operation order of the specification (no
 // fused multiply-add).
@@ -506,10 +511,11 @@ __device__ __forceinline__ uint32_t live_mask(int j, int r0, int n, int w) {
 }
 
 // Row buffer layout: FP32 rows hold each coordinate twice (x0 x0 x1 x1 ...)
-// for the packed L2 path, once otherwise; FP64 rows hold m doubles.
+// for the packed L2 and L-infinity paths, once for L1; FP64 rows hold m
+// doubles.
 template <int M, int NORM, bool F64>
 __host__ __device__ constexpr int tile_row_elems() {
-  return F64 ? M : (NORM == 1 ? ((2 * M + 3) / 4) * 4 : ((M + 3) / 4) * 4);
+  return F64 ? M : (NORM != 2 ? ((2 * M + 3) / 4) * 4 : ((M + 3) / 4) * 4);
 }
 
 // Shared-memory bytes of the tile kernel for a launch shape.
@@ -529,7 +535,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             int* __restrict__ queue) {
   using T = typename std::conditional<F64, double, float>::type;
   constexpr int RE = tile_row_elems<M, NORM, F64>();
-  constexpr bool PACKED = !F64 && NORM == 1 && (C % 2 == 0);
+  constexpr bool PACKED = !F64 && NORM != 2 && (C % 2 == 0);  // L2 and L-infinity
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NW = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5;
@@ -684,7 +690,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             const float4* src = reinterpret_cast<const float4*>(xe + (int64_t)i * mp);
             float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(rowbuf) + lane * RE);
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if constexpr (NORM == 1) {
+            if constexpr (NORM != 2) {
 #pragma unroll
               for (int p = 0; p < (RE / 4 + 1) / 2; ++p) {
                 const float4 v = i < n ? src[p] : z4;
@@ -741,7 +747,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             Nw[c] = 0;
             mn[c] = __int_as_float(0x7f800000);
           }
-          if constexpr (PACKED) {
+          if constexpr (PACKED && NORM == 1) {
             // L2, two columns per packed op.  Accumulate -thr + sum d^2, the
             // exact negation of pair_margin() (round-to-nearest is symmetric),
             // whose sign bit is 1 for a recurrence.  An exact zero (a tie) is
@@ -764,6 +770,39 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
                 }
                 float a0, a1;
                 f2_unpack(acc, a0, a1);
+                Nw[2 * c] = __funnelshift_l(__float_as_uint(a0), Nw[2 * c], 1);
+                Nw[2 * c + 1] = __funnelshift_l(__float_as_uint(a1), Nw[2 * c + 1], 1);
+                mn[2 * c] = min3f(mn[2 * c], fabsf(a0), fabsf(a1));
+              }
+            }
+#pragma unroll
+            for (int c = 0; c < C / 2; ++c) mn[2 * c + 1] = mn[2 * c];
+          } else if constexpr (PACKED) {
+            // L-infinity, two columns per packed subtraction: the exact
+            // maximum of |d_k| per column, then mx - thr, the exact negation
+            // of pair_margin()'s thr - mx, whose sign bit is 1 for a
+            // recurrence.  An exact zero (a tie) is inside the band.
+            const unsigned long long thr2 = f2_pack(thr, thr);
+#pragma unroll 4
+            for (int t = 31; t >= 0; --t) {
+              unsigned long long xr2[M];
+              const float* rb = reinterpret_cast<const float*>(rowbuf) + t * RE;
+#pragma unroll
+              for (int k = 0; k < M; ++k)
+                xr2[k] = *reinterpret_cast<const unsigned long long*>(rb + 2 * k);
+#pragma unroll
+              for (int c = 0; c < C / 2; ++c) {
+                float m0 = 0.f, m1 = 0.f;
+#pragma unroll
+                for (int k = 0; k < M; k += 2) {
+                  float a, b, a2 = 0.f, b2 = 0.f;
+                  f2_unpack(f2_sub(xr2[k], xc2[c][k]), a, b);
+                  if (k + 1 < M) f2_unpack(f2_sub(xr2[k + 1], xc2[c][k + 1]), a2, b2);
+                  m0 = max3f(m0, fabsf(a), fabsf(a2));
+                  m1 = max3f(m1, fabsf(b), fabsf(b2));
+                }
+                float a0, a1;
+                f2_unpack(f2_sub(f2_pack(m0, m1), thr2), a0, a1);
                 Nw[2 * c] = __funnelshift_l(__float_as_uint(a0), Nw[2 * c], 1);
                 Nw[2 * c + 1] = __funnelshift_l(__float_as_uint(a1), Nw[2 * c + 1], 1);
                 mn[2 * c] = min3f(mn[2 * c], fabsf(a0), fabsf(a1));
