@@ -177,6 +177,12 @@ __device__ __forceinline__ void emit2(BlockHist& h, const SeriesDesc& S, uint32_
 // (a) and the run touching its left end (z), or one run over the whole
 // segment.  Join them in order; the run left open at column i+1 is the row's
 // end run for the line-of-identity join.
+// Descriptors are read MERGE_AHEAD strips (items) at a time, all loads of
+// a group issued before any is used: the walk along a row or diagonal is
+// sequential, but its addresses follow from the geometry alone, so the
+// loads need not wait on each other.
+constexpr int MERGE_AHEAD = 8;
+
 __global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || S.cross) return;
@@ -189,29 +195,45 @@ __global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd) {
     const int64_t qlast = (n - 2 - i) / sw;
     uint32_t ocol = 0;
     uint64_t olen = 0;
-    for (int64_t Q = 0; Q <= qlast; ++Q) {
-      const int64_t off = strip_offset(n, sw, Q) + i;
-      const uint32_t z = S.row_z[off];
-      const uint32_t zlen = z >> 2, zcol = z & 1u;
-      if (z & 2u) {  // one run over the whole segment
-        if (olen && ocol == zcol) {
-          olen += zlen;
+    int64_t off = i;  // strip_offset(n, sw, Q) + i, advanced strip by strip
+    for (int64_t Q0 = 0; Q0 <= qlast; Q0 += MERGE_AHEAD) {
+      uint32_t zs[MERGE_AHEAD], as[MERGE_AHEAD];
+#pragma unroll
+      for (int u = 0; u < MERGE_AHEAD; ++u) {
+        const int64_t Q = Q0 + u;
+        zs[u] = 0;
+        as[u] = 0;
+        if (Q <= qlast) {
+          zs[u] = S.row_z[off];
+          as[u] = S.row_a[off];
+          off += n - 1 - Q * sw;  // strip Q holds J1(Q) - 1 = n - Q sw - 1 entries
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < MERGE_AHEAD; ++u) {
+        if (Q0 + u > qlast) break;
+        const uint32_t z = zs[u];
+        const uint32_t zlen = z >> 2, zcol = z & 1u;
+        if (z & 2u) {  // one run over the whole segment
+          if (olen && ocol == zcol) {
+            olen += zlen;
+          } else {
+            emit2(h, S, ocol, olen);
+            ocol = zcol;
+            olen = zlen;
+          }
         } else {
-          emit2(h, S, ocol, olen);
+          const uint32_t a = as[u];
+          const uint32_t alen = a >> 1, acol = a & 1u;
+          if (olen && ocol == acol) {
+            emit2(h, S, acol, olen + alen);
+          } else {
+            emit2(h, S, ocol, olen);
+            emit2(h, S, acol, alen);
+          }
           ocol = zcol;
           olen = zlen;
         }
-      } else {
-        const uint32_t a = S.row_a[off];
-        const uint32_t alen = a >> 1, acol = a & 1u;
-        if (olen && ocol == acol) {
-          emit2(h, S, acol, olen + alen);
-        } else {
-          emit2(h, S, ocol, olen);
-          emit2(h, S, acol, alen);
-        }
-        ocol = zcol;
-        olen = zlen;
       }
     }
     S.rowend[i] = (uint32_t)olen | (ocol << 31);
@@ -238,26 +260,85 @@ __global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd) {
   const int64_t H = banded ? S.band_h : n;
   for (int64_t k = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = n - 1 - k;  // entry row of the current item
+    int64_t i = n - 1 - k;  // entry row of the next item (-1: the walk is done)
     uint64_t L = 0;
-    for (;;) {
-      const int64_t Q = (n - 1 - (i + k)) / sw;
-      const int64_t J1 = n - Q * sw, J0 = J1 - sw;
-      const int64_t g = banded ? i / H : 0;
-      const int64_t R0 = g * H, R1 = R0 + H < n ? R0 + H : n;
-      const int64_t off = banded ? S.dia_off[Q * S.nbands + g] : strip_offset(n, sw, Q);
-      const int64_t o = off + k - band_klo(J1, sw, R1);
-      const uint32_t z = S.dia_z[o];
-      if (z & 0x8000u) {
-        L += (z & 0x7FFFu);
-      } else {
-        const uint64_t first = L + S.dia_a[o];
-        if (first) h.add(S, HIST_DIAG, first);
-        L = z & 0x7FFFu;
+    if (!banded) {
+      // one band: the items are the strips Q = 0, 1, ... in order (the
+      // diagonal leaves strip Q through its left edge J0 into strip Q + 1)
+      // and band_klo is 1, so no division is needed
+      int64_t Q = 0, off = 0;  // off = strip_offset(n, sw, Q)
+      while (i >= 0) {
+        int64_t os[MERGE_AHEAD];
+        int cnt = 0;
+#pragma unroll
+        for (int u = 0; u < MERGE_AHEAD; ++u) {
+          os[u] = -1;
+          if (i >= 0) {
+            os[u] = off + k - 1;
+            ++cnt;
+            const int64_t ie = n - (Q + 1) * sw - k;  // J0 - k, the top cell's row
+            off += n - 1 - Q * sw;
+            ++Q;
+            i = ie > 0 ? ie - 1 : -1;
+          }
+        }
+        uint32_t zs[MERGE_AHEAD], as[MERGE_AHEAD];
+#pragma unroll
+        for (int u = 0; u < MERGE_AHEAD; ++u) {
+          zs[u] = os[u] >= 0 ? S.dia_z[os[u]] : 0u;
+          as[u] = os[u] >= 0 ? S.dia_a[os[u]] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < MERGE_AHEAD; ++u) {
+          if (u >= cnt) break;
+          const uint32_t z = zs[u];
+          if (z & 0x8000u) {
+            L += (z & 0x7FFFu);
+          } else {
+            const uint64_t first = L + as[u];
+            if (first) h.add(S, HIST_DIAG, first);
+            L = z & 0x7FFFu;
+          }
+        }
       }
-      const int64_t ie = R0 > J0 - k ? R0 : J0 - k;  // the diagonal's top cell in the item
-      if (ie <= 0) break;
-      i = ie - 1;
+    }
+    while (i >= 0) {
+      // the next items' descriptor positions, from the geometry alone
+      int64_t os[MERGE_AHEAD];
+      int cnt = 0;
+#pragma unroll
+      for (int u = 0; u < MERGE_AHEAD; ++u) {
+        os[u] = -1;
+        if (i >= 0) {
+          const int64_t Q = (n - 1 - (i + k)) / sw;
+          const int64_t J1 = n - Q * sw, J0 = J1 - sw;
+          const int64_t g = banded ? i / H : 0;
+          const int64_t R0 = g * H, R1 = R0 + H < n ? R0 + H : n;
+          const int64_t off = banded ? S.dia_off[Q * S.nbands + g] : strip_offset(n, sw, Q);
+          os[u] = off + k - band_klo(J1, sw, R1);
+          ++cnt;
+          const int64_t ie = R0 > J0 - k ? R0 : J0 - k;  // the diagonal's top cell in the item
+          i = ie > 0 ? ie - 1 : -1;
+        }
+      }
+      uint32_t zs[MERGE_AHEAD], as[MERGE_AHEAD];
+#pragma unroll
+      for (int u = 0; u < MERGE_AHEAD; ++u) {
+        zs[u] = os[u] >= 0 ? S.dia_z[os[u]] : 0u;
+        as[u] = os[u] >= 0 ? S.dia_a[os[u]] : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < MERGE_AHEAD; ++u) {
+        if (u >= cnt) break;
+        const uint32_t z = zs[u];
+        if (z & 0x8000u) {
+          L += (z & 0x7FFFu);
+        } else {
+          const uint64_t first = L + as[u];
+          if (first) h.add(S, HIST_DIAG, first);
+          L = z & 0x7FFFu;
+        }
+      }
     }
     if (L) h.add(S, HIST_DIAG, L);
   }
