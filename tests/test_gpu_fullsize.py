@@ -14,6 +14,8 @@
     histograms;
   - 200,000 decisions R_ij, drawn uniformly, near the line of identity and
     near the radius, equal the oracle's FP64 decisions one by one.
+* The largest series the library accepts, n = 2^22: the same properties and
+  sampled decisions; one vector more is refused with RQA_ETOOBIG.
 * The paper's timing series (Sect. 8.2, sin over 1,000,001 points, m = 2,
   tau = 2, eps = 1, no Theiler window): the line of identity is one line of
   length n, and the diagonal histogram is otherwise even (both triangles).
@@ -135,3 +137,46 @@ def test_paper_sine_series():
     L = np.arange(n + 1, dtype=np.uint64)
     assert int((L * hd).sum()) == int((L * hv).sum()) == meas["recurrence_points"]
     assert int((L * hw).sum()) == n * n - meas["recurrence_points"]
+
+
+def test_max_size_series():
+    """n = RQA_MAX_N = 2^22 vectors (include/rqa.h), the largest series the
+    library accepts: about 8.8e12 pairs and 69 GB of strip-boundary
+    descriptors.  The same size-independent properties as above hold, and
+    sampled decisions (uniform, near the line of identity, near the radius)
+    equal the oracle's; one vector more is rejected."""
+    max_n = 1 << 22
+    m, tau = 3, 1
+    s = synth.ar1(max_n + (m - 1) * tau, 1009, 0.95)
+    p = dict(m=m, tau=tau, eps=0.5, norm=1, theiler=1)
+    r = gp.RQA(gp.Settings(**p))
+    meas = r.run(s)
+    hd, hv, hw = r.histograms()
+    st = r.stats()
+    n = max_n
+    assert st["n_vec"] == n and meas["n_vec"] == n
+    L = np.arange(n + 1, dtype=np.uint64)
+    rp = int((L * hv).sum())
+    assert int((L * hd).sum()) == rp == meas["recurrence_points"] > 0
+    assert int((L * hw).sum()) == n * n - rp
+    assert hd[0] == hv[0] == hw[0] == 0 and int(hd.sum()) % 2 == 0
+    assert st["exact"] == 1
+    rng = np.random.default_rng(7)
+    i = rng.integers(0, n, 6_000)
+    j = rng.integers(0, n, 6_000)
+    k = rng.integers(0, 40, 3_000)
+    i2 = rng.integers(0, n - 40, 3_000)
+    pi = rng.integers(0, n, 400_000)
+    pj = rng.integers(0, n, 400_000)
+    x = np.stack([s[pi + q * tau] - s[pj + q * tau] for q in range(m)])
+    near = np.argsort(np.abs(np.sqrt((x * x).sum(axis=0)) - p["eps"]))[:3_000]
+    i = np.concatenate([i, i2, pi[near]])
+    j = np.concatenate([j, i2 + k, pj[near]])
+    got = r.sample(i, j)
+    want = np.array([oracle.distance(s, a, b, m, tau, p["norm"]) <= p["eps"]
+                     and abs(a - b) >= p["theiler"] for a, b in zip(i, j)], dtype=np.uint8)
+    assert np.array_equal(got, want)
+    r.close()
+    with pytest.raises(gp.RQAError) as e:
+        gp.RQA(gp.Settings(**p)).run(np.concatenate([s, [0.0]]))
+    assert e.value.status == 9  # RQA_ETOOBIG
