@@ -203,3 +203,38 @@ def test_medium_lorenz_streaming_oracle():
     x = synth.lorenz_x(20_000, 1)
     y = synth.lorenz_x(15_000, 2)
     check_cross(x, y, m=5, tau=3, eps=0.3, norm=0, theiler=5)
+
+
+def test_max_rows_rectangle():
+    """n1 = RQA_MAX_N = 2^22 row vectors against n2 = 2^20 column vectors
+    (4.4e12 cells): every cell lies in exactly one vertical black or white
+    run of its column, the diagonal and vertical scans see the same
+    recurrence points, and sampled decisions (uniform and near the radius)
+    equal the oracle's."""
+    m, tau, eps, norm, w = 3, 1, 0.5, 1, 1
+    x = synth.ar1((1 << 22) + (m - 1) * tau, 1011, 0.95)
+    y = synth.ar1((1 << 20) + (m - 1) * tau, 1013, 0.95)
+    r = gp.RQA(gpu_settings(m, tau, eps, norm, w))
+    meas = r.run_cross(x, y)
+    hd, hv, hw = r.histograms()
+    st = r.stats()
+    n1, n2 = 1 << 22, 1 << 20
+    assert st["mode"] == 1 and st["n_vec"] == n1 and st["n_cols"] == n2
+    L = np.arange(len(hd), dtype=np.uint64)
+    rp = int((L * hv).sum())
+    assert int((L * hd).sum()) == rp == meas["recurrence_points"] > 0
+    assert int((L * hw).sum()) == n1 * n2 - rp
+    assert st["exact"] == 1
+    rng = np.random.default_rng(11)
+    i = rng.integers(0, n1, 6000)
+    j = rng.integers(0, n2, 6000)
+    pi = rng.integers(0, n1, 400_000)
+    pj = rng.integers(0, n2, 400_000)
+    d = np.sqrt(sum((x[pi + q * tau] - y[pj + q * tau]) ** 2 for q in range(m)))
+    near = np.argsort(np.abs(d - eps))[:3000]
+    i = np.concatenate([i, pi[near]])
+    j = np.concatenate([j, pj[near]])
+    got = r.sample(i, j)
+    want = np.array([abs(a - b) >= w and oracle.cross_distance(x, y, a, b, m, tau, norm) <= eps
+                     for a, b in zip(i, j)], dtype=np.uint8)
+    assert np.array_equal(got, want)
