@@ -225,35 +225,6 @@ __device__ __forceinline__ uint32_t scan2(uint32_t x, int hi, int lo, uint32_t s
   return (cl + (uint32_t)(top - lo + 1)) | (col << 28) | (fl << 29);
 }
 
-// Scan the black runs of cells hi..lo (descending; x already restricted to
-// seg, their mask), continuing diagonal state st.  first(len) receives the
-// run that touches the strip's edge when it ends (len may be 0), emit(len)
-// every other run that ends inside (interior runs straight to the shared
-// bins: a black run consists of live cells of one word).
-template <class E, class F>
-__device__ __forceinline__ uint32_t scan_black(uint32_t x, uint32_t seg, int hi, int lo,
-                                               uint32_t st, const HistSink& hs, E&& emit,
-                                               F&& first) {
-  const uint32_t z = ~x & seg;
-  const uint32_t cl = st & ST_LEN;
-  if (z == 0) return (cl + (uint32_t)(hi - lo + 1)) | (st & DG_EDGE);
-  const int ptop = msb(z);
-  const uint32_t f = cl + (uint32_t)(hi - ptop);
-  if (st & DG_EDGE)
-    first(f);
-  else if (f)
-    emit(f);
-  const int pbot = __ffs(z) - 1;
-  uint32_t mid = x & lowmask(ptop) & ~lowmask(pbot + 1);
-  while (mid) {
-    const int h = msb(mid);
-    const int zz = msb(z & lowmask(h));
-    hs.add_in(HIST_DIAG, (uint32_t)(h - zz));
-    mid &= lowmask(zz);
-  }
-  return (uint32_t)(pbot - lo);
-}
-
 // Lines of length 1..3 are counted without emitting them one by one: 16-bit
 // fields packed two per register, added to the histograms every
 // FLUSH_BLOCKS blocks (at most 128 per field per block, so no field wraps).
@@ -310,9 +281,16 @@ __device__ __forceinline__ uint32_t scan2_full(uint32_t x, uint32_t st, ShortCou
   return (uint32_t)(__ffs(T) - 1) | ((x & 1u) << 28);
 }
 
-// Black-run scan of a full word (cells 31 .. 0), same contract as
-// scan_black(x, FULL, 31, 0, ...), with interior runs of length 1..3
-// counted by popcounts as in scan2_full.
+// Black-run scan of a full word (cells 31 .. 0), continuing diagonal state
+// st.  first(len) receives the run that touches the strip's edge when it
+// ends (len may be 0), emit(len) every other run that ends at the word's
+// top; interior runs of length 1..3 are counted by popcounts as in
+// scan2_full, longer ones go straight to the shared bins.  The black run
+// left open at cell 0 is returned.  A segment of a word (cells hi..lo) is
+// scanned as a full word whose cells outside the segment are black: they
+// extend only the run left open at the bottom, whose length the caller
+// shortens by their number (the cells below the segment; those above it are
+// moved out by a shift first).
 template <class E, class F>
 __device__ __forceinline__ uint32_t scanb_full(uint32_t x, uint32_t st, ShortCounts& sc,
                                                const HistSink& hs, E&& emit, F&& first) {
@@ -980,8 +958,10 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
               if (k >= klo) dia_a[off + k - klo] = (uint16_t)len;
             };
             if (c == C - 1) {
-              // upper segment only (bits 31..d), entering from the right
-              dU_new[c * 32 + lane] = scan_black(D & segU, segU, 31, d, dL, hs, emitd, firstd);
+              // upper segment only (bits 31..d), entering from the right;
+              // its d cells below count as black and are taken off again
+              dU_new[c * 32 + lane] =
+                  scanb_full(D | segL, dL, sc, hs, emitd, firstd) - (uint32_t)d;
             } else {
               // the lower segment of sub-block c+1 (bits d-1..0 of Dprev) and
               // the upper segment of c (bits 31..d of D) are one diagonal;
@@ -998,13 +978,14 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           const int k = jw0 - r0 + d - 32;
           const uint32_t du = dU_old[lane];
           dL = du;
-          if (d > 0)
-            dL = scan_black(
-                Dprev & segL, segL, d - 1, 0, du, hs,
-                [&](uint32_t len) { hs.add(HIST_DIAG, len); },
-                [&](uint32_t len) {
-                  if (k >= klo) dia_a[off + k - klo] = (uint16_t)len;
-                });
+          if (d > 0)  // the segment shifted to the top, 32 - d black cells below it
+            dL = scanb_full(
+                     (Dprev << (32 - d)) | lowmask(32 - d), du, sc, hs,
+                     [&](uint32_t len) { hs.add(HIST_DIAG, len); },
+                     [&](uint32_t len) {
+                       if (k >= klo) dia_a[off + k - klo] = (uint16_t)len;
+                     }) -
+                 (uint32_t)(32 - d);
           hs.drain(lane);
         }
         bufo ^= 1;
