@@ -20,8 +20,21 @@
 namespace rqa {
 
 // ----------------------------------------------------------------- prepare
-__global__ void prepare_kernel(SeriesDesc* __restrict__ sd) {
-  SeriesDesc& S = sd[blockIdx.x];
+// A double as an unsigned integer with the same order (finite values).
+__device__ __forceinline__ unsigned long long ordered_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_ordered_bits(unsigned long long o) {
+  return __longlong_as_double((long long)((o >> 63) ? (o & 0x7FFFFFFFFFFFFFFFull) : ~o));
+}
+
+// Minimum, maximum and non-finite check of series blockIdx.y (and, for cross
+// recurrence, of the second series), blockIdx.x taking a grid-stride share:
+// min and max are order-independent, so combining the blocks by atomic
+// maxima of the encoded values is deterministic.
+__global__ void prepare_scan_kernel(SeriesDesc* __restrict__ sd) {
+  SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.s || !S.counters) return;  // nothing to prepare
   __shared__ double s_mn[32], s_mx[32];
   __shared__ int s_bad[32];
@@ -30,7 +43,8 @@ __global__ void prepare_kernel(SeriesDesc* __restrict__ sd) {
   // cross recurrence: both series share one centre and scale, so FP32
   // differences of a row and a column vector are differences of the values
   const int64_t total = S.cross ? S.N + S.N2 : S.N;
-  for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
     const double v = i < S.N ? S.s[i] : S.s2[i - S.N];
     if (!isfinite(v)) {
       bad = 1;
@@ -39,7 +53,6 @@ __global__ void prepare_kernel(SeriesDesc* __restrict__ sd) {
       mx = fmax(mx, v);
     }
   }
-  // min, max and or are order-independent, so the reduction is deterministic
   for (int o = 16; o > 0; o >>= 1) {
     mn = fmin(mn, __shfl_xor_sync(FULL, mn, o));
     mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
@@ -58,13 +71,23 @@ __global__ void prepare_kernel(SeriesDesc* __restrict__ sd) {
     mx = fmax(mx, s_mx[w]);
     bad |= s_bad[w];
   }
-  mn = fmin(mn, s_mn[0]);
-  mx = fmax(mx, s_mx[0]);
-  bad |= s_bad[0];
-  if (bad) {
-    atomicExch(&S.counters[CNT_STATUS], 3ull /* RQA_ENAN */);
-    return;
+  if (bad) atomicExch(&S.counters[CNT_STATUS], 3ull /* RQA_ENAN */);
+  if (mn <= mx) {  // the block saw a finite value
+    atomicMax(&S.counters[CNT_LO], ~ordered_bits(mn));
+    atomicMax(&S.counters[CNT_HI], ordered_bits(mx));
   }
+}
+
+// Centre, scale, FP32 radius and proven error band of each series, from the
+// minimum and maximum prepare_scan_kernel gathered (one thread per series).
+__global__ void prepare_kernel(SeriesDesc* __restrict__ sd, int count) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  SeriesDesc& S = sd[q];
+  if (S.n <= 0 || !S.s || !S.counters) return;
+  if (S.counters[CNT_STATUS] == 3ull) return;  // non-finite input
+  const double mn = from_ordered_bits(~S.counters[CNT_LO]);
+  const double mx = from_ordered_bits(S.counters[CNT_HI]);
   // Centre on the mid-range (minimises max |s - c|) and scale by a power of
   // two so the FP32 copies lie in [-1, 1].
   const double center = 0.5 * mn + 0.5 * mx;
@@ -783,8 +806,12 @@ void launch_wait_selftest(unsigned long long* status, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------ host launch
-void launch_prepare(SeriesDesc* d_sd, int count, cudaStream_t st) {
-  prepare_kernel<<<count, 256, 0, st>>>(d_sd);
+void launch_prepare(SeriesDesc* d_sd, int count, int64_t max_len, int sms, cudaStream_t st) {
+  int64_t blocks = (max_len + 8191) / 8192;  // 32 values per thread
+  if (blocks > 4 * sms) blocks = 4 * sms;
+  if (blocks < 1) blocks = 1;
+  prepare_scan_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+  prepare_kernel<<<(count + 127) / 128, 128, 0, st>>>(d_sd, count);
 }
 void launch_embed(SeriesDesc* d_sd, int count, int64_t max_n_mp, int sms, cudaStream_t st) {
   int64_t blocks = (max_n_mp + 255) / 256;
@@ -812,6 +839,7 @@ __global__ void last_bin_kernel(SeriesDesc* sd) {
 
 int preload_aux_kernels() {
   const void* fns[] = {
+      reinterpret_cast<const void*>(prepare_scan_kernel),
       reinterpret_cast<const void*>(prepare_kernel),
       reinterpret_cast<const void*>(embed_kernel),
       reinterpret_cast<const void*>(merge_rows_kernel),

@@ -486,7 +486,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   using Key = std::tuple<int, int, int, int, int>;  // m, norm, f64, warps, cross
   std::map<Key, int> cls_of;
   std::vector<Key> classes;
-  int64_t max_n_mp = 0, total_items = 0;
+  int64_t max_n_mp = 0, total_items = 0, max_len = 0;
   bool any_fp32 = false;
   for (int q = 0; q < count; ++q) {
     std::string msg;
@@ -555,6 +555,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       max_n_mp = std::max(max_n_mp, (p.z.n + (p.z.cross ? p.z.n2 : 0)) * p.z.mp);
     }
     total_items += p.z.nitems;
+    max_len = std::max(max_len, in[q].N + (in[q].cross ? in[q].N2 : 0));
   }
   const int ncls = static_cast<int>(classes.size());
   if (ncls == 0) {  // nothing runnable: report the first validation failure
@@ -856,8 +857,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
         (e = cudaMemcpyAsync(arena_ + o_series0, host_ + h_series, series_bytes,
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync(series)");
-    launch_prepare(d_sd, nrun, st);
-    ++launches;
+    launch_prepare(d_sd, nrun, max_len, sms_, st);
+    launches += 2;
     if (any_fp32) {
       launch_embed(d_sd, nrun, max_n_mp, sms_, st);
       ++launches;

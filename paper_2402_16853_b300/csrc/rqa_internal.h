@@ -65,10 +65,19 @@ __host__ __device__ inline void desc_set_symmetric(SeriesDesc& d) {
 }
 
 enum { HIST_DIAG = 0, HIST_VERT = 1, HIST_WHITE = 2 };
-// Per-series counters: rechecks, status, and (written after the merges) the
+// Per-series counters: rechecks, status, (written after the merges) the
 // longest length with a non-zero count in each of the three histograms, so
-// the host reads each histogram only up to there.
-enum { CNT_RECHECKS = 0, CNT_STATUS = 1, CNT_LAST = 2 /* [3] */, CNT_WORDS = 5 };
+// the host reads each histogram only up to there, and the series' minimum
+// and maximum in an order-preserving encoding (the minimum complemented),
+// gathered by atomic maxima while the series is scanned.
+enum {
+  CNT_RECHECKS = 0,
+  CNT_STATUS = 1,
+  CNT_LAST = 2 /* [3] */,
+  CNT_LO = 5,
+  CNT_HI = 6,
+  CNT_WORDS = 7
+};
 
 // Offset of strip Q's descriptors: strips hold J1(Q) - 1 entries each, with
 // J1(Q) = n - Q*sw the exclusive right end of the strip.

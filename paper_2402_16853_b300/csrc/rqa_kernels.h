@@ -25,7 +25,8 @@ TileFn tile_kernel_cross_norm2(int m, int cols, bool f64, bool bands);
 // Line detection over a precomputed bit matrix (no distances).
 TileFn tile_kernel_matrix(int cols, bool bands = false);
 
-void launch_prepare(SeriesDesc* d_sd, int count, cudaStream_t st);
+// max_len: the longest series (both series for cross recurrence) of the set
+void launch_prepare(SeriesDesc* d_sd, int count, int64_t max_len, int sms, cudaStream_t st);
 void launch_embed(SeriesDesc* d_sd, int count, int64_t max_n_mp, int sms, cudaStream_t st);
 // The merge and finalize kernels; `sym` / `cross` say whether the set holds
 // RQA series (rows, diagonals, line-of-identity join) and cross-recurrence

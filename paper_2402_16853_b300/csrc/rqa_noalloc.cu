@@ -193,7 +193,7 @@ extern "C" int rqa_run_noalloc(const rqa_settings* settings, const double* dev_s
           cudaSuccess)
     return fail(RQA_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   noalloc_setup_kernel<<<1, 256, 0, st>>>(d_sd, d_items, static_cast<int>(nstrips), init);
-  launch_prepare(d_sd, 1, st);
+  launch_prepare(d_sd, 1, init.N, sms, st);
   if (!f64) launch_embed(d_sd, 1, n * mp, sms, st);
   if (nstrips > 0) {
     TileFn fn = tile_kernel_for(s.m, s.norm, tc.cols, f64, false);

@@ -106,7 +106,7 @@ int plot_common(const rqa_settings* settings, const double* host_x, int64_t nx,
                                      cudaMemcpyHostToDevice, st)) != cudaSuccess)) {
     rc = plot_fail(RQA_ECUDA, cudaGetErrorString(e));
   } else {
-    launch_prepare(d_sd, 1, st);
+    launch_prepare(d_sd, 1, nx + (cross ? ny : 0), sms, st);
     if (!f64) launch_embed(d_sd, 1, (n + (cross ? n2 : 0)) * mp, sms, st);
     launch_plot(d_sd, i0, j0, rows, cols, d_out, f64 ? 1 : 0, settings->m, settings->norm, sms,
                 st);

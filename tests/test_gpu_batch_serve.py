@@ -205,10 +205,10 @@ def test_served_banded_requests_equal_alone():
 def test_preload_kernels_once_per_process():
     """Every tile kernel instantiation (m = 1..10, three norms, FP32 and FP64,
     RQA and cross, with and without row bands, and the two matrix-input
-    ones) plus the ten preparation and merge kernels are loaded; a second
+    ones) plus the eleven preparation and merge kernels are loaded; a second
     call finds them loaded and reports the same count."""
     n = gp.preload_kernels()
-    assert n == 10 * 3 * 2 * 2 * 2 + 2 + 10
+    assert n == 10 * 3 * 2 * 2 * 2 + 2 + 11
     assert gp.preload_kernels() == n
     # a run afterwards is unaffected
     s = synth.ar1(600, 5, 0.9)
