@@ -59,3 +59,28 @@ def test_invalid_settings_rejected_before_device_lookup():
     with pytest.raises(rqa_pkg.RQAError) as ei:
         rqa_pkg.RQA(rqa_pkg.Settings(m=11, tau=1, eps=0.5))
     assert ei.value.status == 9  # RQA_ETOOBIG
+
+
+def test_batch_marshalling_dtypes_match_the_c_structs():
+    """Batch.run passes numpy arrays where the ABI wants arrays of
+    rqa_settings and rqa_measures_t: their dtypes must have the structs'
+    field names, offsets, sizes and types."""
+    import ctypes
+
+    import numpy as np
+
+    from paper_2402_16853_b300 import rqa as R
+    kinds = {ctypes.c_int32: np.int32, ctypes.c_int64: np.int64, ctypes.c_double: np.float64}
+    for cls, dt in ((R._CSettings, R._SETTINGS_DT), (R._CMeasures, R._MEASURES_DT)):
+        assert dt.itemsize == ctypes.sizeof(cls)
+        assert list(dt.names) == [f for f, _ in cls._fields_]
+        for f, t in cls._fields_:
+            assert dt.fields[f][1] == getattr(cls, f).offset
+            assert dt.fields[f][0] == np.dtype(kinds[t])
+    assert list(R._MEASURES_DT.names) == R.MEASURE_FIELDS
+    # a round trip through the C layout
+    a = np.zeros(2, R._SETTINGS_DT)
+    a["m"] = [3, 7]
+    a["eps"] = [0.5, 0.25]
+    c = (R._CSettings * 2).from_buffer_copy(a.tobytes())
+    assert (c[0].m, c[1].m, c[0].eps, c[1].eps) == (3, 7, 0.5, 0.25)
