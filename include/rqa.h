@@ -155,8 +155,9 @@ int rqa_create(const rqa_settings* settings, rqa_handle** out);
  * are owned by the handle and reused by later runs of the same or smaller n. */
 int rqa_run(rqa_handle* h, const double* host_series, int64_t n);
 
-/* Run on a series already on the device (e.g. a torch CUDA tensor), ordered
- * on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
+/* The run of Sect. 7.4 (RQAComputation.run) on a series already in device
+ * memory (e.g. a torch CUDA tensor), ordered on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  The
  * caller keeps the series alive and unmodified until the call returns; the
  * call returns when the results are on the host. */
 int rqa_run_device(rqa_handle* h, const double* dev_series, int64_t n,
@@ -192,17 +193,25 @@ int rqa_run_matrix(rqa_handle* h, const uint32_t* host_bits, int64_t rows,
  * cuda_stream. */
 int rqa_run_matrix_device(rqa_handle* h, const uint32_t* dev_bits, int64_t rows,
                           int64_t cols, void* cuda_stream);
-/* Copy the measures of the last successful run. */
+/* Copy the measures of the last successful run: the members of the
+ * paper's RQAResult object (Sect. 7.4, e.g. determinism; Table 3 lists
+ * them), computed from the three line-length distributions as defined
+ * above (the paper defers the definitions to Marwan et al. 2007, Sect. 2).
+ * RQA_EINVAL if there is no successful run. */
 int rqa_measures(const rqa_handle* h, rqa_measures_t* out);
 
-/* Copy a histogram of the last run: kind 0 = diagonal lines, 1 = vertical
- * lines, 2 = white vertical lines; entry l = number of lines of length l,
+/* Copy a histogram of the last run -- one of the frequency distributions of
+ * the three line types that Sect. 2 names (diagonal lines and vertical lines
+ * of recurrence points, white vertical lines of non-recurrence points):
+ * kind 0 = diagonal lines, 1 = vertical lines, 2 = white vertical lines;
+ * entry l = number of lines of length l,
  * l = 0..n (entry 0 is always 0; cross recurrence: l = 0..max(n1, n2)).
  * cap = capacity of `out` in entries; *len receives n + 1.  RQA_EINVAL if cap < n + 1 (then *len still says how
  * many entries are needed). */
 int rqa_histogram(const rqa_handle* h, int32_t kind, uint64_t* out,
                   int64_t cap, int64_t* len);
 
+/* Diagnostics of the last run (rqa_stats_t); the paper has no counterpart. */
 int rqa_stats(const rqa_handle* h, rqa_stats_t* out);
 
 /* Evaluate individual recurrence decisions R_ij of the last run's series
@@ -214,8 +223,15 @@ int rqa_stats(const rqa_handle* h, rqa_stats_t* out);
 int rqa_sample_decisions(rqa_handle* h, const int64_t* i, const int64_t* j,
                          int64_t count, uint8_t* out);
 
+/* End a computation made by rqa_create (Sect. 7.3): frees its device
+ * buffers and the handle.  NULL is ignored. */
 void rqa_destroy(rqa_handle* h);
 
+/* Failures are status codes here where PyRQA raises exceptions (Sect. 6:
+ * an absent compute device makes its execution throw).  rqa_strerror()
+ * names a code (a static string; "unknown status" for other values);
+ * rqa_last_error() gives the detail of the last failure on a handle (valid
+ * until the handle's next call). */
 const char* rqa_strerror(int status);
 const char* rqa_last_error(const rqa_handle* h);
 
@@ -240,10 +256,18 @@ const char* rqa_last_error(const rqa_handle* h);
  * Series of more than RQA_NOALLOC_MAX_N embedded vectors are rejected with
  * RQA_ETOOBIG before anything is launched.  All calls share the one array:
  * calls whose work overlaps on the GPU (other streams, other host threads)
- * race and must be serialised by the caller.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make it before
- * any stream capture.  rqa_noalloc_last_error() describes the last failure
- * of the calling thread. */
+ * race and must be serialised by the caller.  The call always blocks until
+ * its work on cuda_stream has finished (it reads a status word back), so it
+ * must not be called on a stream that is being captured into a CUDA graph.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), which also loads the module holding the array if
+ * CUDA's lazy loading has not yet done so; rqa_preload_kernels() performs
+ * that look-up ahead of time.  settings->theiler at or above n acts as n
+ * (every cell removed).  settings->band_override must be negative (the
+ * automatic, exact band) or +inf (every pair re-decided in FP64); other
+ * values are refused with RQA_EINVAL, since this call has no statistics
+ * through which to report an inexact result.  rqa_noalloc_last_error()
+ * describes the last failure of the calling thread. */
 #define RQA_NOALLOC_MAX_N ((int64_t)32768)
 #define RQA_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 int rqa_run_noalloc(const rqa_settings* settings, const double* dev_series,
@@ -314,7 +338,8 @@ int rqa_probe_alu(int32_t kind, double* ops_per_s);
  * launch, and a load can stall the whole context while other work runs.
  * rqa_preload_kernels() loads every kernel a run can launch (all tile kernel
  * instantiations and the preparation and merge kernels) into the current
- * device's context, once per process; later calls return at once.
+ * device's context and resolves the device address of rqa_run_noalloc's
+ * static scratch array, once per process; later calls return at once.
  * *loaded (may be NULL) receives the number of kernels it loaded.
  * rqa_server_create calls it.  RQA_ENODEV without an sm_103 device,
  * RQA_ECUDA if a load fails. */
@@ -333,6 +358,24 @@ int rqa_batch_create(rqa_batch** out);
 int rqa_batch_run(rqa_batch* b, const rqa_settings* settings,
                   const double* const* series, const int64_t* lens,
                   int32_t count, rqa_measures_t* out, int32_t* status);
+/* The batched run in the shape of a single call (no batch object to
+ * manage): series q (lens[q] FP64 values in host memory) is analysed with
+ * settings[q] -- `settings` holds one entry per series, so a uniform batch
+ * repeats one set of parameters -- and out[q] receives its measures (zeroed
+ * if the series failed).  The device work is ordered on `stream` (a
+ * cudaStream_t, NULL = the library's own stream): it starts after work
+ * already queued there and the call returns once the results are on the
+ * host.  The work queue, CUDA graph and device buffers are those of
+ * rqa_batch_run, held in a batch object that belongs to the calling host
+ * thread and is reused by its later calls (repeated shapes replay the
+ * captured graph) until rqa_run_batch_release() frees it.  Returns RQA_OK
+ * if every series succeeded, else the first failing status. */
+int rqa_run_batch(const rqa_settings* settings, const double* const* series,
+                  const int64_t* lens, int32_t count, rqa_measures_t* out,
+                  void* stream);
+/* Free the calling thread's rqa_run_batch buffers (a later call recreates
+ * them). */
+void rqa_run_batch_release(void);
 /* Histogram of series q of the last batch run (same layout as
  * rqa_histogram). */
 int rqa_batch_histogram(const rqa_batch* b, int32_t q, int32_t kind,
@@ -341,7 +384,9 @@ int rqa_batch_stats(const rqa_batch* b, rqa_stats_t* out);
 void rqa_batch_destroy(rqa_batch* b);
 
 /* ----------------------------------------------------------------- served
- * Continuous batching.  Requests are admitted while their device memory
+ * The paper has no counterpart: it runs one computation at a time
+ * (Sect. 7.3-7.4).  This is the same computation served to many callers
+ * with continuous batching.  Requests are admitted while their device memory
  * (series, embedded vectors, descriptors, histograms) fits in
  * mem_budget_bytes and a slot is free; admitted requests are batched into
  * launch epochs as they arrive, so work of requests that arrive while others
@@ -349,13 +394,20 @@ void rqa_batch_destroy(rqa_batch* b);
  * boundary state on the device until it completes. */
 typedef struct rqa_server rqa_server;
 
+/* Create a server with a device-memory budget (bytes) and at most
+ * max_slots requests in flight; *out receives it.  Loads every kernel first
+ * (rqa_preload_kernels).  RQA_ENODEV without an sm_103 device. */
 int rqa_server_create(size_t mem_budget_bytes, int32_t max_slots,
                       rqa_server** out);
-/* Copy the series and queue the request; *ticket identifies it. */
+/* Copy the series and queue the request (an RQAComputation.run of Sect. 7.4
+ * with its own Settings); *ticket identifies it.  RQA_EINVAL for invalid
+ * settings, RQA_ESHORT / RQA_ETOOBIG for series that cannot run, RQA_ENOMEM
+ * if the request alone exceeds the server's budget. */
 int rqa_submit(rqa_server* s, const rqa_settings* settings,
                const double* host_series, int64_t n, uint64_t* ticket);
 /* RQA_PENDING until done; then the request's status, with *out filled on
- * RQA_OK.  A finished ticket may be polled until rqa_release(). */
+ * RQA_OK (the request's RQAResult, Sect. 7.4).  A finished ticket may be
+ * polled until rqa_release(); RQA_ENOTFOUND for an unknown ticket. */
 int rqa_poll(rqa_server* s, uint64_t ticket, rqa_measures_t* out);
 /* Block until the ticket finishes or timeout_ms passes (RQA_PENDING). */
 int rqa_wait(rqa_server* s, uint64_t ticket, int64_t timeout_ms,
@@ -367,6 +419,8 @@ int rqa_release(rqa_server* s, uint64_t ticket);
 int rqa_server_counters(rqa_server* s, int64_t* admitted, int64_t* completed,
                         int64_t* queued, int64_t* in_flight,
                         int64_t* bytes_in_use, int64_t* epochs);
+/* Stop the server: waits for the requests in flight, drops queued ones and
+ * frees every buffer.  NULL is ignored. */
 void rqa_server_destroy(rqa_server* s);
 
 #ifdef __cplusplus

@@ -249,7 +249,9 @@ int rqa_preload_kernels(int32_t* loaded) {
   const uint64_t bit = dev < 64 ? (1ull << dev) : 0;
   if (!(done & bit)) {
     const int t = rqa::preload_tile_kernels();
-    const int a = t < 0 ? -1 : rqa::preload_aux_kernels();
+    const int a0 = t < 0 ? -1 : rqa::preload_aux_kernels();
+    const int z = a0 < 0 ? -1 : rqa::preload_noalloc();
+    const int a = z < 0 ? -1 : a0 + z;
     if (t < 0 || a < 0) {
       cudaGetLastError();
       return RQA_ECUDA;
@@ -290,8 +292,10 @@ int rqa_selftest_bounded_wait(int32_t* status, int64_t* cycles_waited) {
   return h[2] == 1 ? RQA_OK : RQA_ECUDA;  // the abort flag must be raised
 }
 
-int rqa_batch_run(rqa_batch* b, const rqa_settings* settings, const double* const* series,
-                  const int64_t* lens, int32_t count, rqa_measures_t* out, int32_t* status) {
+namespace {
+int batch_run_on(rqa_batch* b, const rqa_settings* settings, const double* const* series,
+                 const int64_t* lens, int32_t count, rqa_measures_t* out, int32_t* status,
+                 cudaStream_t stream) {
   if (!b || count < 0 || (count > 0 && (!settings || !series || !lens))) return RQA_EINVAL;
   std::vector<rqa::SeriesInput> in(count);
   for (int32_t q = 0; q < count; ++q) {
@@ -299,7 +303,7 @@ int rqa_batch_run(rqa_batch* b, const rqa_settings* settings, const double* cons
     in[q].host = series[q];
     in[q].N = lens[q];
   }
-  int rc = b->eng->run(in, b->res, nullptr, true);
+  int rc = b->eng->run(in, b->res, stream, true);
   b->err = b->eng->error();
   b->stats = rqa_stats_t{};
   for (int32_t q = 0; q < count && q < static_cast<int32_t>(b->res.size()); ++q) {
@@ -323,6 +327,40 @@ int rqa_batch_run(rqa_batch* b, const rqa_settings* settings, const double* cons
   b->stats.kernel_ms = b->eng->last_tile_ms();
   b->stats.total_ms = b->eng->last_total_ms();
   return rc;
+}
+
+// The batch object behind rqa_run_batch: one per host thread and device,
+// kept for reuse (its buffers and captured graph) until rqa_run_batch_release.
+thread_local rqa_batch* t_run_batch = nullptr;
+thread_local int t_run_batch_dev = -1;
+}  // namespace
+
+int rqa_batch_run(rqa_batch* b, const rqa_settings* settings, const double* const* series,
+                  const int64_t* lens, int32_t count, rqa_measures_t* out, int32_t* status) {
+  return batch_run_on(b, settings, series, lens, count, out, status, nullptr);
+}
+
+int rqa_run_batch(const rqa_settings* settings, const double* const* series, const int64_t* lens,
+                  int32_t count, rqa_measures_t* out, void* stream) {
+  if (count < 0 || (count > 0 && (!settings || !series || !lens || !out))) return RQA_EINVAL;
+  std::string msg;
+  int dev = 0;
+  int rc = find_device(&dev, &msg);
+  if (rc != RQA_OK) return rc;
+  if (t_run_batch && t_run_batch_dev != dev) rqa_run_batch_release();
+  if (!t_run_batch) {
+    rc = rqa_batch_create(&t_run_batch);
+    if (rc != RQA_OK) return rc;
+    t_run_batch_dev = dev;
+  }
+  return batch_run_on(t_run_batch, settings, series, lens, count, out, nullptr,
+                      static_cast<cudaStream_t>(stream));
+}
+
+void rqa_run_batch_release(void) {
+  if (t_run_batch) rqa_batch_destroy(t_run_batch);
+  t_run_batch = nullptr;
+  t_run_batch_dev = -1;
 }
 
 int rqa_batch_histogram(const rqa_batch* b, int32_t q, int32_t kind, uint64_t* out, int64_t cap,

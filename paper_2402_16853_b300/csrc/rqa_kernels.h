@@ -43,6 +43,9 @@ void launch_wait_selftest(unsigned long long* status, cudaStream_t st);
 // rqa_preload_kernels); the count loaded, or -1 on a CUDA error.
 int preload_tile_kernels();
 int preload_aux_kernels();
+// Resolves the address of rqa_run_noalloc's static scratch on the current
+// device and loads its kernel (1, or -1 on a CUDA error).
+int preload_noalloc();
 void launch_sample(const SeriesDesc* d_sd, const int64_t* ii, const int64_t* jj, int64_t count,
                    uint8_t* out, int f64, cudaStream_t st);
 

@@ -23,9 +23,18 @@
 //     GPU (different streams, different host threads) race and corrupt each
 //     other: serialise them;
 //   * the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress; make that first call before any stream capture.
+//     cudaGetSymbolAddress, which loads this file's module (and with it the
+//     array) if CUDA's lazy loading has not done so yet; rqa_preload_kernels()
+//     does the same look-up ahead of time, so that no later call pays for it;
+//   * every call blocks until its work on the stream has finished (it reads
+//     the status word back), so it must not be issued on a stream that is
+//     being captured into a CUDA graph;
+//   * only the automatic recheck band (band_override < 0) or rechecking every
+//     pair (band_override = +inf) is accepted: with no statistics to return,
+//     a call could not report a result made inexact by a narrower band.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -98,6 +107,24 @@ int fail(int code, const std::string& msg) {
 
 }  // namespace
 
+namespace rqa {
+// Resolves the scratch address on the current device and loads this file's
+// kernel, so that the first rqa_run_noalloc() call does no module loading.
+// Returns the number of kernels loaded, or -1 on a CUDA error.
+int preload_noalloc() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  void* p = nullptr;
+  std::string msg;
+  if (scratch_base(dev, &p, &msg) != RQA_OK) return -1;
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(noalloc_setup_kernel)) !=
+      cudaSuccess)
+    return -1;
+  return 1;
+}
+}  // namespace rqa
+
 extern "C" const char* rqa_noalloc_last_error(void) { return t_last_error.c_str(); }
 
 extern "C" int rqa_run_noalloc(const rqa_settings* settings, const double* dev_series,
@@ -111,6 +138,10 @@ extern "C" int rqa_run_noalloc(const rqa_settings* settings, const double* dev_s
       s.norm < 0 || s.norm > 2 || s.theiler < 0 || s.l_min < 1 || s.v_min < 1 || s.w_min < 1 ||
       s.precision < 0 || s.precision > 2 || s.band_override != s.band_override)
     return fail(RQA_EINVAL, "invalid settings");
+  if (s.band_override >= 0.0 && s.band_override != __builtin_inf())
+    return fail(RQA_EINVAL,
+                "rqa_run_noalloc accepts band_override < 0 (automatic band) or +inf only: it "
+                "cannot report a result made inexact by a narrower band");
   if (s.m > RQA_MAX_M) return fail(RQA_ETOOBIG, "embedding dimension above RQA_MAX_M");
   const int64_t n = n_points - static_cast<int64_t>(s.m - 1) * s.tau;
   if (n_points < 1 || n < 1) return fail(RQA_ESHORT, "series shorter than the embedding window");
@@ -169,7 +200,9 @@ extern "C" int rqa_run_noalloc(const rqa_settings* settings, const double* dev_s
   init.m = s.m;
   init.tau = s.tau;
   init.norm = s.norm;
-  init.w = s.theiler;
+  // a window of n or more removes every cell, as any wider one does; capping
+  // it keeps the kernels' index arithmetic (j - w - r0) inside int range
+  init.w = static_cast<int32_t>(std::min<int64_t>(s.theiler, n));
   init.mp = mp;
   init.sw = static_cast<int32_t>(sw);
   init.eps = s.eps;

@@ -80,6 +80,14 @@ __device__ __forceinline__ int clamp32(int v) { return v < 0 ? 0 : (v > 32 ? 32 
 // Position of the highest set bit (x != 0).
 __device__ __forceinline__ int msb(uint32_t x) { return 31 - __clz(x); }
 
+// Position of the lowest set bit (x != 0): the highest set bit of the
+// isolated lowest bit, one bfind instead of a bit reverse and a find.
+__device__ __forceinline__ uint32_t lowbit_index(uint32_t x) {
+  uint32_t r;
+  asm("bfind.u32 %0, %1;" : "=r"(r) : "r"(x & (0u - x)));
+  return r;
+}
+
 // 32 x 32 bit transpose across a warp: lane r holds row r (bit c = A[r][c]);
 // on return lane c holds bit r = A[r][c].  Five stages; each swaps the
 // off-diagonal j x j blocks of every 2j x 2j block with one shuffle and, for
@@ -272,13 +280,19 @@ __device__ __forceinline__ uint32_t scan2_full(uint32_t x, uint32_t st, ShortCou
     sc.v3w1 += __popc(l3 & x) + (__popc(l1 & ~x) << 16);
     sc.w23 += __popc(l2 & ~x) + (__popc(l3 & ~x) << 16);
     uint32_t lg = S & ~(t1 | t2 | t3);
-    while (lg) {  // q < ptop, so T >> (q + 1) still holds the run's upper end
-      const int q = __ffs(lg) - 1;
-      lg &= lg - 1;
-      hs.add_in(((x >> q) & 1u) ? HIST_VERT : HIST_WHITE, (uint32_t)__ffs(T >> (q + 1)));
+    while (lg) {
+      // lowest cell q of a run of length >= 4 whose upper end is a transition
+      // below bit 32: in the word of the run's colour as ones, adding 2^q
+      // carries through the run and stops at that transition, so the bits
+      // that change are the run plus one
+      const uint32_t bq = lg & (0u - lg);
+      lg ^= bq;
+      const bool black = (x & bq) != 0u;
+      const uint32_t y = black ? x : ~x;
+      hs.add_in(black ? HIST_VERT : HIST_WHITE, (uint32_t)__popc((y + bq) ^ y) - 1u);
     }
   }
-  return (uint32_t)(__ffs(T) - 1) | ((x & 1u) << 28);
+  return lowbit_index(T) | ((x & 1u) << 28);
 }
 
 // Black-run scan of a full word (cells 31 .. 0), continuing diagonal state
@@ -309,13 +323,13 @@ __device__ __forceinline__ uint32_t scanb_full(uint32_t x, uint32_t st, ShortCou
     sc.d12 += __popc(Sb & t1) + (__popc(Sb & t2 & ~t1) << 16);
     sc.d3 += __popc(Sb & t3 & ~(t1 | t2));
     uint32_t lg = Sb & ~(t1 | t2 | t3);
-    while (lg) {  // q < zt, so T >> (q + 1) still holds the run's upper end
-      const int q = __ffs(lg) - 1;
-      lg &= lg - 1;
-      hs.add_in(HIST_DIAG, (uint32_t)__ffs(T >> (q + 1)));
+    while (lg) {  // as in scan2_full: the carry from bit q runs through the black run
+      const uint32_t bq = lg & (0u - lg);
+      lg ^= bq;
+      hs.add_in(HIST_DIAG, (uint32_t)__popc((x + bq) ^ x) - 1u);
     }
   }
-  return (uint32_t)(__ffs(~x) - 1);
+  return lowbit_index(~x);
 }
 
 // Add a warp's short-line counters to the CTA's shared bins and clear them.
@@ -733,11 +747,15 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             const unsigned long long nthr2 = f2_pack(-thr, -thr);
 #pragma unroll 4
             for (int t = 31; t >= 0; --t) {
-              unsigned long long xr2[M];
-              const float* rb = reinterpret_cast<const float*>(rowbuf) + t * RE;
+              unsigned long long xr2[2 * (RE / 4)];
+              const ulonglong2* rb =
+                  reinterpret_cast<const ulonglong2*>(reinterpret_cast<const float*>(rowbuf) + t * RE);
 #pragma unroll
-              for (int k = 0; k < M; ++k)
-                xr2[k] = *reinterpret_cast<const unsigned long long*>(rb + 2 * k);
+              for (int p = 0; p < RE / 4; ++p) {  // 16-byte loads: two coordinates each
+                const ulonglong2 v = rb[p];
+                xr2[2 * p] = v.x;
+                xr2[2 * p + 1] = v.y;
+              }
 #pragma unroll
               for (int c = 0; c < C / 2; ++c) {
                 unsigned long long acc = nthr2;
@@ -763,11 +781,15 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             const unsigned long long thr2 = f2_pack(thr, thr);
 #pragma unroll 4
             for (int t = 31; t >= 0; --t) {
-              unsigned long long xr2[M];
-              const float* rb = reinterpret_cast<const float*>(rowbuf) + t * RE;
+              unsigned long long xr2[2 * (RE / 4)];
+              const ulonglong2* rb =
+                  reinterpret_cast<const ulonglong2*>(reinterpret_cast<const float*>(rowbuf) + t * RE);
 #pragma unroll
-              for (int k = 0; k < M; ++k)
-                xr2[k] = *reinterpret_cast<const unsigned long long*>(rb + 2 * k);
+              for (int p = 0; p < RE / 4; ++p) {  // 16-byte loads: two coordinates each
+                const ulonglong2 v = rb[p];
+                xr2[2 * p] = v.x;
+                xr2[2 * p + 1] = v.y;
+              }
 #pragma unroll
               for (int c = 0; c < C / 2; ++c) {
                 float m0 = 0.f, m1 = 0.f;

@@ -134,6 +134,9 @@ def load(path: str = LIB_PATH):
         "rqa_batch_histogram": (c.c_int, [vp, c.c_int32, c.c_int32, P(c.c_uint64), c.c_int64,
                                           P(c.c_int64)]),
         "rqa_batch_stats": (c.c_int, [vp, P(_CStats)]),
+        "rqa_run_batch": (c.c_int, [P(_CSettings), P(P(c.c_double)), P(c.c_int64), c.c_int32,
+                                    P(_CMeasures), vp]),
+        "rqa_run_batch_release": (None, []),
         "rqa_batch_destroy": (None, [vp]),
         "rqa_server_create": (c.c_int, [c.c_size_t, c.c_int32, P(vp)]),
         "rqa_submit": (c.c_int, [vp, P(_CSettings), P(c.c_double), c.c_int64, P(c.c_uint64)]),
@@ -402,6 +405,35 @@ class Batch:
         s = _CStats()
         load().rqa_batch_stats(self._h, ctypes.byref(s))
         return {k: getattr(s, k) for k, _ in _CStats._fields_}
+
+
+def run_batch(settings: Sequence[Settings], series: Sequence[np.ndarray], stream=None):
+    """rqa_run_batch: one call over many host series, device work ordered on
+    `stream` (a torch.cuda.Stream, a raw cudaStream_t as int, or None).
+    Returns (list of measure dicts, None for a failed series; rc)."""
+    k = len(series)
+    if len(settings) != k:
+        raise ValueError("one Settings per series")
+    arrs = [_f64(s) for s in series]
+    cs = np.zeros(k, _SETTINGS_DT)
+    for f in _SETTINGS_DT.names:
+        cs[f] = [getattr(s, f) for s in settings]
+    ptrs = np.fromiter((a.__array_interface__["data"][0] for a in arrs), np.uintp, k)
+    lens = np.fromiter((a.shape[0] for a in arrs), np.int64, k)
+    out = np.zeros(k, _MEASURES_DT)
+    P = ctypes.POINTER
+    raw = getattr(stream, "cuda_stream", stream)
+    rc = load().rqa_run_batch(cs.ctypes.data_as(P(_CSettings)),
+                              ptrs.ctypes.data_as(P(P(ctypes.c_double))),
+                              lens.ctypes.data_as(P(ctypes.c_int64)), k,
+                              out.ctypes.data_as(P(_CMeasures)),
+                              ctypes.c_void_p(raw) if raw else None)
+    res = [dict(zip(MEASURE_FIELDS, row)) for row in out.tolist()]
+    return res, int(rc)
+
+
+def run_batch_release() -> None:
+    load().rqa_run_batch_release()
 
 
 class Server:

@@ -32,6 +32,21 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
+def test_run_batch_has_the_boundary_signature():
+    """rqa_run_batch(const rqa_settings*, const double* const*, const int64_t*,
+    int32_t count, rqa_measures_t* out, void* stream): the batched call with a
+    caller's stream, declared once in the header and exported."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    m = re.search(r"int\s+rqa_run_batch\s*\(([^)]*)\)", src)
+    assert m, "rqa_run_batch not declared"
+    args = [re.sub(r"\s+", " ", a).strip() for a in m.group(1).split(",")]
+    assert args == ["const rqa_settings* settings", "const double* const* series",
+                    "const int64_t* lens", "int32_t count", "rqa_measures_t* out",
+                    "void* stream"], args
+    lib = rqa_pkg.load()
+    assert hasattr(lib, "rqa_run_batch") and hasattr(lib, "rqa_run_batch_release")
+
+
 def test_strerror_names_every_code():
     for code in range(11):
         assert rqa_pkg.strerror(code) != "unknown status"

@@ -205,10 +205,12 @@ def test_served_banded_requests_equal_alone():
 def test_preload_kernels_once_per_process():
     """Every tile kernel instantiation (m = 1..10, three norms, FP32 and FP64,
     RQA and cross, with and without row bands, and the two matrix-input
-    ones) plus the eleven preparation and merge kernels are loaded; a second
-    call finds them loaded and reports the same count."""
+    ones), the eleven preparation and merge kernels and the set-up kernel of
+    the allocation-free entry point (whose static scratch address is
+    resolved at the same time) are loaded; a second call finds them loaded
+    and reports the same count."""
     n = gp.preload_kernels()
-    assert n == 10 * 3 * 2 * 2 * 2 + 2 + 11
+    assert n == 10 * 3 * 2 * 2 * 2 + 2 + 11 + 1
     assert gp.preload_kernels() == n
     # a run afterwards is unaffected
     s = synth.ar1(600, 5, 0.9)
@@ -218,3 +220,59 @@ def test_preload_kernels_once_per_process():
     r.run(s)
     hd, hv, hw = r.histograms()
     assert np.array_equal(hd, want["hd"]) and np.array_equal(hw, want["hw"])
+
+
+def test_batch_cfg4_long_series_equal_oracle():
+    """Series of the batched workload's upper lengths (5,000 to 20,000
+    points): all three generators, m from 2 to 8, all norms, mixed in one
+    batch so that several kernel classes run on the side streams with row
+    bands, plus a short series alone in its class (no row bands).  Every
+    histogram equals the FP64 oracle's."""
+    rng = np.random.default_rng(4242)
+    plan = [("logistic", 8, 19_800, 0), ("lorenz", 5, 12_000, 1), ("ar1", 2, 20_000, 2),
+            ("logistic", 3, 5_100, 1), ("lorenz", 8, 16_000, 0), ("ar1", 7, 9_000, 2),
+            ("ar1", 4, 17_500, 1), ("lorenz", 2, 7_300, 2), ("logistic", 6, 14_000, 0),
+            ("ar1", 3, 400, 0)]
+    specs = [synth.SeriesSpec(kind, L, m, int(rng.integers(1, 5)), norm,
+                              float(rng.uniform(0.05, 0.5)),
+                              float(rng.uniform(3.6, 4.0)) if kind == "logistic"
+                              else float(rng.uniform(0.5, 0.99)) if kind == "ar1" else 0.0)
+             for kind, m, L, norm in plan]
+    series, eps = synth.make_series(specs, 4243)
+    settings = [gp.Settings(m=sp.m, tau=sp.tau, eps=e, norm=sp.norm, theiler=sp.theiler)
+                for sp, e in zip(specs, eps)]
+    b = gp.Batch()
+    res, st, rc = b.run(settings, series)
+    assert rc == 0 and all(x == 0 for x in st)
+    for q, (stg, s) in enumerate(zip(settings, series)):
+        want = _oracle(stg, s)
+        for kind, key in ((0, "hd"), (1, "hv"), (2, "hw")):
+            assert np.array_equal(b.histogram(q, kind), want[key]), (q, key)
+        assert_same_measures(res[q], want["measures"])
+    b.close()
+
+
+def test_run_batch_on_a_caller_stream():
+    """rqa_run_batch (the batched call with the boundary's shape): its
+    device work is ordered after work already queued on the caller's stream,
+    its measures equal those of the batch object and of the oracle, and a
+    second call with the same shapes (graph replay) repeats them."""
+    import torch
+    settings, series = _mixed(24, 77, lo=300, hi=6000)
+    b = gp.Batch()
+    want, st, rc = b.run(settings, series)
+    assert rc == 0
+    b.close()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        busy = torch.empty(1 << 28, dtype=torch.float32, device="cuda")
+        busy.fill_(1.0)   # queued ahead of the batch on the same stream
+    for _ in range(2):
+        got, rc = gp.run_batch(settings, series, stream)
+        assert rc == 0
+        for g, w in zip(got, want):
+            assert_same_measures(g, w)
+    for q in (0, 5, 11):
+        assert_same_measures(got[q], _oracle(settings[q], series[q])["measures"])
+    gp.run_batch_release()
+    del busy
