@@ -61,7 +61,9 @@ def parse():
     ap.add_argument("--no-cross", action="store_true")
     ap.add_argument("--no-sine", action="store_true")
     ap.add_argument("--no-matrix", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--no-saturation", action="store_true",
+                    help="skip the served-rate sweep (16 workers vs one sequential worker)")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--N", type=int, default=0,
                     help="series length override (default: the 1,048,576-point workload)")
@@ -216,6 +218,10 @@ def run_reference(args):
     v = float(np.median(vals))
     step_s = n * n / v
     line = {"impl": "reference", "metric": "recurrence cells/s", "value": v,
+            "extrapolated": True,
+            "extrapolation": "value = cells/s of bounded samples (every k-th column and "
+                             "diagonal); ms_per_step = n^2 / value, the whole matrix at "
+                             "that rate, not a timed full run",
             "unit": "cells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -341,6 +347,10 @@ def run_mine(args):
                               "measures_identical": bool(same)}
         del r64
 
+    # ---- the two smaller single-series workloads (context lines)
+    extra["logistic_n2000"] = bench_single(gp, "logistic_n2000", dev, barrier, flush, peak, 50)
+    extra["lorenz_n100k"] = bench_single(gp, "lorenz_n100k", dev, barrier, flush, peak, 10)
+
     # ---- cross recurrence of two AR(1) series (context line)
     if not args.no_cross:
         extra["cross"] = bench_cross(gp, params, dev, barrier, flush, peak)
@@ -398,6 +408,41 @@ def run_mine(args):
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def bench_single(gp, name, dev, barrier, flush, peak, steps):
+    """One of the smaller single-series workloads on a device-resident series:
+    cells/s per step (L2 flushed before each), and the tile kernel's share of
+    the ALU roofline as for the primary line."""
+    import torch
+    s, p = synth.workload(name)
+    t = torch.tensor(s, dtype=torch.float64, device=dev)
+    r = gp.RQA(gp.Settings(**p))
+    for _ in range(3):
+        r.run(t)
+    barrier()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    kms = []
+    e0.record(stream)
+    for _ in range(steps):
+        flush.fill_(1)
+        r.run(t)
+        kms.append(r.stats()["kernel_ms"])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sec = e0.elapsed_time(e1) / 1e3 / steps
+    st = r.stats()
+    n = st["n_vec"]
+    k_ms = float(np.median(kms))
+    ops = st["pairs"] * (2 * p["m"] + 1)
+    return {"workload": f"{name}: N = {len(s)}, m = {p['m']}, tau = {p['tau']}, "
+                        f"norm {p['norm']}, eps = {p['eps']}, w = {p['theiler']}",
+            "value": float(n) * n / sec, "unit": "cells/s", "ms_per_step": sec * 1e3,
+            "steps": steps, "kernel_ms": k_ms, "roofline_frac": ops / (k_ms / 1e3) / 1e12 / peak,
+            "band_rows": int(st["band_rows"]), "strip_width": int(st["strip_width"]),
+            "l2": "flushed before every timed step (512 MiB write)"}
 
 
 def bench_cross(gp, params, dev, barrier, flush, peak, N=524_288, steps=2):
@@ -508,6 +553,7 @@ def bench_batch(gp, args, dev, barrier):
     settings = [gp.Settings(m=sp.m, tau=sp.tau, eps=e, norm=sp.norm, theiler=sp.theiler,
                             l_min=sp.l_min, v_min=sp.v_min, w_min=sp.w_min)
                 for sp, e in zip(specs, eps)]
+    tuned = gp.tuning_table_loaded()
     b = gp.Batch()
     res, status, rc = b.run(settings, series)   # captures the graph
     assert rc == 0, status
@@ -519,14 +565,20 @@ def bench_batch(gp, args, dev, barrier):
         res2, st2, rc2 = b.run(settings, series)
     t_batch = (time.perf_counter() - t0) / steps
     bst = b.stats()
-    # sequential single-series calls of the same kernels
+    # sequential single-series calls of the same kernels on one prebuilt
+    # handle (rqa_set_settings between series), its buffers already grown to
+    # the largest series, so only the per-series launch work is timed
+    rr = gp.RQA(settings[0])
+    big = max(range(len(series)), key=lambda q: len(series[q]))
+    rr.set_settings(settings[big])
+    rr.run(series[big])
     t0 = time.perf_counter()
     seq = []
     for stg, s in zip(settings, series):
-        rr = gp.RQA(stg)
+        rr.set_settings(stg)
         seq.append(rr.run(s))
-        rr.close()
     t_seq = time.perf_counter() - t0
+    rr.close()
     same = all(a == bb or (isinstance(a, float) and math.isnan(a) and math.isnan(bb))
                for m1, m2 in zip(res2, seq) for a, bb in zip(m1.values(), m2.values()))
     cells = float(sum((len(s) - (sp.m - 1) * sp.tau) ** 2 for s, sp in zip(series, specs)))
@@ -535,30 +587,70 @@ def bench_batch(gp, args, dev, barrier):
             "kernel_ms": bst["kernel_ms"], "device_ms": bst["total_ms"],
             "sequential_series_per_s": len(series) / t_seq,
             "speedup_vs_sequential": t_seq / t_batch, "identical_to_sequential": bool(same),
-            "graph": "captured once, replayed"}
+            "sequential_baseline": "rqa_run per series on one prebuilt handle "
+                                   "(rqa_set_settings between series)",
+            "tuned": tuned,
+            "graph": "captured once, replayed",
+            "cpu_oracle": batch_oracle_sample(specs, series, eps) if not args.no_cpu else None}
 
 
-def bench_serve(gp, args):
-    arrivals, specs, series, eps = synth.serve_stream(duration=args.serve_seconds)
-    settings = [gp.Settings(m=sp.m, tau=sp.tau, eps=e, norm=sp.norm, theiler=sp.theiler,
-                            l_min=sp.l_min, v_min=sp.v_min, w_min=sp.w_min)
-                for sp, e in zip(specs, eps)]
-    srv = gp.Server(40 << 30, max_slots=4096)
-    # warm the engines
-    t = srv.submit(settings[0], series[0])
+def batch_oracle_sample(specs, series, eps, every=64):
+    """The FP64 oracle on every 64th series of the batch, one series after
+    another on all host cores (streaming mode): series/s and cells/s."""
+    import oracle
+    cores = os.cpu_count() or 1
+    idx = list(range(0, len(series), every))
+    cells = 0.0
+    t0 = time.perf_counter()
+    for q in idx:
+        sp = specs[q]
+        st = oracle.Settings(m=sp.m, tau=sp.tau, eps=eps[q], norm=sp.norm, theiler=sp.theiler,
+                             l_min=sp.l_min, v_min=sp.v_min, w_min=sp.w_min)
+        oracle.rqa(series[q], st, mode="streaming", threads=cores)
+        n = len(series[q]) - (sp.m - 1) * sp.tau
+        cells += float(n) * n
+    dt = time.perf_counter() - t0
+    return {"series_per_s": len(idx) / dt, "cells_per_s": cells / dt, "cores": cores,
+            "kind": "oracle", "sample": f"every {every}-th series of the batch "
+                                         f"({len(idx)} series, {dt:.1f} s)"}
+
+
+def serve_stream_run(gp, arrivals, settings, series, cells_per_req, seconds,
+                     workers=None, epoch_cells=None, drain_s=120.0):
+    """Replay a Poisson request stream against a fresh server (optionally with
+    RQA_SERVE_WORKERS / RQA_SERVE_EPOCH_CELLS overrides) and measure each
+    request from submission to completion.  Requests still pending drain_s
+    after the last arrival count as not served."""
+    env = {}
+    if workers is not None:
+        env["RQA_SERVE_WORKERS"] = str(workers)
+    if epoch_cells is not None:
+        env["RQA_SERVE_EPOCH_CELLS"] = repr(float(epoch_cells))
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        srv = gp.Server(40 << 30, max_slots=4096)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    t = srv.submit(settings[0], series[0])   # warm the engines
     srv.wait(t)
     srv.release(t)
-    lat = [None] * len(series)
-    done_at = [None] * len(series)
-    tickets = [None] * len(series)
+    k_all = len(series)
+    done_at = [None] * k_all
+    tickets = [None] * k_all
+    submit_at = [None] * k_all
+    stop = threading.Event()
     t0 = time.perf_counter()
-    submit_at = [None] * len(series)
 
     def poller():
         pending = set()
         q = 0
-        while q < len(series) or pending:
-            while q < len(series) and tickets[q] is not None:
+        while q < k_all or pending:
+            while q < k_all and tickets[q] is not None:
                 pending.add(q)
                 q += 1
             fin = []
@@ -570,6 +662,8 @@ def bench_serve(gp, args):
             for k in fin:
                 pending.discard(k)
                 srv.release(tickets[k])
+            if stop.is_set() and q >= k_all:
+                break
             if not fin:
                 time.sleep(0.0005)
 
@@ -581,19 +675,68 @@ def bench_serve(gp, args):
             time.sleep(a - now)
         submit_at[k] = time.perf_counter()
         tickets[k] = srv.submit(stg, s)
+    deadline = time.perf_counter() + drain_s
+    while th.is_alive() and time.perf_counter() < deadline:
+        th.join(timeout=0.5)
+    stop.set()
     th.join()
-    t_end = max(done_at)
-    lat = np.array([d - s0 for d, s0 in zip(done_at, submit_at)])
-    cells = float(sum((len(s) - (sp.m - 1) * sp.tau) ** 2 for s, sp in zip(series, specs)))
-    ctr = srv.counters()
-    srv.close()
+    srv.close()   # waits for epochs in flight, drops what is still queued
+    done = [q for q in range(k_all) if done_at[q] is not None]
+    lat = np.array([done_at[q] - submit_at[q] for q in done])
+    t_end = max(done_at[q] for q in done)
     wall = t_end - t0
-    return {"requests": len(series), "offered_rate_per_s": len(series) / args.serve_seconds,
-            "series_per_s": len(series) / wall, "cells_per_s": cells / wall,
+    return {"requests": k_all, "completed": len(done),
+            "offered_rate_per_s": k_all / seconds,
+            "series_per_s": len(done) / wall,
+            "cells_per_s": float(sum(cells_per_req[q] for q in done)) / wall,
             "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "max_ms": float(lat.max() * 1e3), "epochs": ctr["epochs"],
-            "budget_bytes": 40 << 30, "seconds_of_arrivals": args.serve_seconds}
+            "max_ms": float(lat.max() * 1e3)}
+
+
+def bench_serve(gp, args):
+    """cfg5: Poisson arrivals at 200 req/s for --serve-seconds (60 s by
+    default, about 12,000 requests), lengths log-uniform in [1,000, 200,000],
+    memory admission under a 40 GB budget.  Then a rate sweep (8 s per rate)
+    against the same server and against one worker that runs one request per
+    launch epoch (sequential plain launches): the highest offered rate each
+    sustains with p99 under 100 ms and every request served."""
+    def stream(rate, seconds, seed):
+        arrivals, specs, series, eps = synth.serve_stream(rate=rate, duration=seconds, seed=seed)
+        settings = [gp.Settings(m=sp.m, tau=sp.tau, eps=e, norm=sp.norm, theiler=sp.theiler,
+                                l_min=sp.l_min, v_min=sp.v_min, w_min=sp.w_min)
+                    for sp, e in zip(specs, eps)]
+        cells = [float(len(s) - (sp.m - 1) * sp.tau) ** 2 for s, sp in zip(series, specs)]
+        return arrivals, settings, series, cells
+
+    arrivals, settings, series, cells = stream(200.0, args.serve_seconds, 1005)
+    out = serve_stream_run(gp, arrivals, settings, series, cells, args.serve_seconds)
+    out.update({"budget_bytes": 40 << 30, "seconds_of_arrivals": args.serve_seconds,
+                "workers": 16})
+    if not args.no_saturation:
+        sweep = []
+        for rate in (200.0, 400.0, 800.0):
+            arr, stg, ser, cl = stream(rate, 8.0, 3005)
+            row = {"offered_rate_per_s": rate}
+            for name, w, ec in (("continuous_16_workers", None, None),
+                                ("sequential_1_worker", 1, 1.0)):
+                r = serve_stream_run(gp, arr, stg, ser, cl, 8.0, workers=w, epoch_cells=ec,
+                                     drain_s=30.0)
+                row[name] = {k: r[k] for k in ("completed", "requests", "series_per_s",
+                                               "p50_ms", "p99_ms")}
+            sweep.append(row)
+
+        def sustained(name):
+            ok = [row["offered_rate_per_s"] for row in sweep
+                  if row[name]["completed"] == row[name]["requests"]
+                  and row[name]["p99_ms"] < 100.0]
+            return max(ok) if ok else None
+        out["rate_sweep_8s"] = sweep
+        out["sustained_rate_p99_under_100ms"] = {"continuous_16_workers":
+                                                 sustained("continuous_16_workers"),
+                                                 "sequential_1_worker":
+                                                 sustained("sequential_1_worker")}
+    return out
 
 
 def main():

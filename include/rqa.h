@@ -149,6 +149,13 @@ typedef struct rqa_handle rqa_handle;
  * there is none of compute capability 10.3).  *out receives the handle. */
 int rqa_create(const rqa_settings* settings, rqa_handle** out);
 
+/* Replace the handle's analysis parameters (a new Settings object for the
+ * same computation object, Sect. 7.2-7.3) without giving up its device
+ * buffers, streams or loaded kernels, so that a sequence of series with
+ * different parameters runs on one handle.  RQA_EINVAL (settings kept) if
+ * they are invalid; the previous result is forgotten. */
+int rqa_set_settings(rqa_handle* h, const rqa_settings* settings);
+
 /* Run on a host series of n FP64 values (RQAComputation.run, Sect. 7.4).
  * The library copies the series to the device (pageable or pinned host
  * memory both work) and blocks until the result is ready.  Device buffers
@@ -297,21 +304,40 @@ const char* rqa_plot_last_error(void);
 /* --------------------------------------------------------------- autotuner
  * Sect. 9 plans the automatic selection of the best-performing
  * implementation at runtime.  rqa_autotune() times whole runs (device time
- * from the first copy to the last) for each CTA-strip width (1, 2, 4 and 8 warps; 128 columns per warp) on one series
+ * from the first copy to the last) for each tile shape -- CTA-strip width
+ * (1, 2, 4 and 8 warps), columns per lane (4, or 2 for FP32 distances) and
+ * row-band height -- on one series
  * -- host_series of n_points values, or a built-in z-scored AR(1) series of
  * n_points values when host_series is NULL -- as RQA (cross = 0) or as the
  * cross recurrence of the series with itself (cross = 1), and records the
- * fastest width for the class (RQA or cross, m, norm, FP64 or not,
+ * fastest shape for the class (RQA or cross, m, norm, FP64 or not,
  * ceil(log2 n)).  Every later run of that class in the process (single,
- * cross, batched, served) uses the recorded width; results do not depend on
+ * cross, batched, served) uses the recorded shape; results do not depend on
  * it.  *best_warps receives the width; ms_per_width (4 floats, may be NULL)
- * the best of two timed runs per width.  rqa_autotune_clear() forgets every
- * recorded width.  The environment variable RQA_TILE_WARPS (1..8) overrides
- * the table.  rqa_autotune_last_error() describes the last failure of the
+ * the best of two timed runs per width at four columns per lane.
+ * rqa_autotune_clear() forgets every recorded shape.  The environment
+ * variables RQA_TILE_WARPS (1..8) and RQA_TILE_COLS (2 or 4) override the
+ * table.  rqa_autotune_last_error() describes the last failure of the
  * calling thread. */
 int rqa_autotune(const rqa_settings* settings, const double* host_series,
                  int64_t n_points, int32_t cross, int32_t* best_warps,
                  float* ms_per_width);
+/* The full tile-shape search for the same class: every strip width at four
+ * and (FP32 distances only) two columns per lane, and, when the winner runs
+ * in row bands, the band height of the size rule halved and doubled.  The
+ * winner is recorded for the class as by rqa_autotune; *best_warps,
+ * *best_cols (2 or 4), *best_band_scale (-1, 0, +1) and *best_ms (whole-run
+ * device time) receive it (any pointer may be NULL).  rqa_autotune searches
+ * this space too but reports only the width. */
+int rqa_autotune_shape(const rqa_settings* settings, const double* host_series,
+                       int64_t n_points, int32_t cross, int32_t* best_warps,
+                       int32_t* best_cols, int32_t* best_band_scale, float* best_ms);
+/* Write the recorded choices to a text file (one class per line: kind m norm
+ * f64 log2n warps cols band_scale), or read such a file and record its
+ * entries, overriding the classes it names (*entries, may be NULL, receives
+ * their number).  A malformed file records nothing and returns RQA_EINVAL. */
+int rqa_autotune_save(const char* path);
+int rqa_autotune_load(const char* path, int32_t* entries);
 void rqa_autotune_clear(void);
 const char* rqa_autotune_last_error(void);
 /* ------------------------------------------------------ failure self-test

@@ -68,18 +68,47 @@ class _CMeasures(ctypes.Structure):
 MEASURE_FIELDS = [f for f, _ in _CMeasures._fields_]
 
 
+def _host_id() -> str:
+    """CPU model and feature flags of this host: -march=native code built on
+    one CPU may not run on another, so the library is rebuilt when they
+    change (the repository is copied between machines with its build
+    folder)."""
+    model = flags = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if not model and line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                elif not flags and line.startswith("flags"):
+                    flags = line.split(":", 1)[1].strip()
+                if model and flags:
+                    break
+    except OSError:
+        pass
+    import hashlib
+    return hashlib.sha256((model + "|" + flags).encode()).hexdigest()
+
+
 def build(force: bool = False) -> str:
-    """Compile rqa_oracle.c into a shared library (gcc, OpenMP, no FMA)."""
+    """Compile rqa_oracle.c into a shared library (gcc -O3 -march=native,
+    OpenMP, no FMA contraction, no fast-math: every FP64 operation is the
+    IEEE one the source writes, in the source's order)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    stamp = _LIB + ".host"
+    host = _host_id()
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)
+            and os.path.exists(stamp) and open(stamp).read() == host):
         return _LIB
     tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", "-std=c11", "-Wall", "-Wextra", _SRC, "-o", tmp,
-           "-lm"]
+    cmd = ["gcc", "-O3", "-march=native", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-Wall", "-Wextra", _SRC,
+           "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
+    with open(stamp + f".{os.getpid()}.tmp", "w") as f:
+        f.write(host)
+    os.replace(stamp + f".{os.getpid()}.tmp", stamp)
     return _LIB
 
 

@@ -105,6 +105,20 @@ int rqa_create(const rqa_settings* settings, rqa_handle** out) {
   return RQA_OK;
 }
 
+int rqa_set_settings(rqa_handle* h, const rqa_settings* settings) {
+  if (!h) return RQA_EINVAL;
+  std::string msg;
+  const int rc = rqa::validate_settings(settings, &msg);
+  if (rc != RQA_OK) {
+    h->err = msg;
+    return rc;
+  }
+  h->st = *settings;
+  h->have = false;  // the last result no longer matches the settings
+  h->err.clear();
+  return RQA_OK;
+}
+
 static int run_input(rqa_handle* h, std::vector<rqa::SeriesInput>& in, void* stream) {
   std::vector<rqa::SeriesResult> res;
   int rc = h->eng->run(in, res, static_cast<cudaStream_t>(stream), false);

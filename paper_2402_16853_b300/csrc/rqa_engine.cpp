@@ -97,14 +97,18 @@ struct Sizes {
 // 7,104 warps (two per resident warp slot of the 80-register kernel on 148
 // SMs) -- about 2,048 items of at least 128 rows.  `rows` is the number of
 // rows summed over the strips.
-int64_t band_rows_for(int64_t n, int64_t rows, int64_t nstrips, int warps) {
+int64_t band_rows_for(int64_t n, int64_t rows, int64_t nstrips, int warps, int band_scale) {
   if (const char* e = std::getenv("RQA_BAND_ROWS")) {
     const int64_t h = std::atoll(e);
     return h > 0 ? (h + 31) / 32 * 32 : 0;
   }
   if (n < 512 || nstrips * warps >= 7104) return 0;
-  const int64_t h = (rows + 2047) / 2048;
-  return std::max<int64_t>(128, (h + 31) / 32 * 32);
+  int64_t h = (rows + 2047) / 2048;
+  h = std::max<int64_t>(128, (h + 31) / 32 * 32);
+  // the autotuner may halve or double the rule's height (never below 64 rows)
+  if (band_scale < 0) h = std::max<int64_t>(64, (h / 2 + 31) / 32 * 32);
+  if (band_scale > 0) h *= 2;
+  return h;
 }
 
 // Visit the items (Q, g) of a banded series with the rows they hold and the
@@ -134,7 +138,7 @@ void for_each_band_item(const Sizes& z, F&& f) {
 // precomputed N x N2 bit matrix (its copy counted in `series`).
 Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross = false,
                 int64_t N2 = 0, bool copy_series2 = false, bool matrix = false,
-                int warps = 0, bool allow_bands = false) {
+                int warps = 0, bool allow_bands = false, int cols = 0) {
   Sizes z;
   z.matrix = matrix;
   z.n = matrix ? N : nvec_of(st, N);
@@ -145,6 +149,9 @@ Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross 
   z.mp = (z.f64 || matrix) ? 0 : ((st.m + 3) / 4) * 4;
   z.tc = choose_tile(z.n2, st.m, st.norm, z.f64, matrix ? 2 : cross ? 1 : 0);
   if (warps > 0) z.tc.warps = warps;
+  if (cols > 0) z.tc.cols = cols;
+  // two columns per lane exist for the FP32 distance kernels only
+  if (z.f64 || matrix) z.tc.cols = 4;
   const int64_t sw = 32LL * z.tc.warps * z.tc.cols;
   if (z.cross) {
     z.nstrips = cross_num_strips(z.n2, sw);
@@ -156,7 +163,8 @@ Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross 
   }
   {
     const int64_t rows = z.cross ? z.n * z.nstrips : z.nrowdesc;  // rows over all strips
-    const int64_t h = allow_bands ? band_rows_for(z.n, rows, z.nstrips, z.tc.warps) : 0;
+    const int64_t h =
+        allow_bands ? band_rows_for(z.n, rows, z.nstrips, z.tc.warps, z.tc.band_scale) : 0;
     if (h > 0 && h < z.n) {
       z.band_h = h;
       z.nbands = (z.n + h - 1) / h;
@@ -307,19 +315,25 @@ int validate_settings(const rqa_settings* st, std::string* msg) {
 }
 
 TileConfig choose_tile(int64_t n, int m, int norm, bool f64, int kind) {
-  TileConfig c{1, 4};
+  TileConfig c{1, 4, 0};
   if (n >= 65536)
     c.warps = 8;
   else if (n >= 16384)
     c.warps = 4;
   else if (n >= 4096)
     c.warps = 2;
-  if (const int t = tune_lookup(kind, m, norm, f64, n)) c.warps = t;
+  TileConfig t{};
+  if (tune_lookup(kind, m, norm, f64, n, &t)) c = t;
   if (const char* e = std::getenv("RQA_TILE_WARPS")) {
     const int w = std::atoi(e);
     if (w >= 1 && w <= 8) c.warps = w;
   }
-  if (const int f = tune_forced_warps()) c.warps = f;
+  if (const char* e = std::getenv("RQA_TILE_COLS")) {
+    const int k = std::atoi(e);
+    if (k == 2 || k == 4) c.cols = k;
+  }
+  tune_apply_forced(&c);
+  if (f64 || kind == 2) c.cols = 4;  // two columns per lane: FP32 distances only
   return c;
 }
 
@@ -329,7 +343,7 @@ size_t series_device_bytes(const rqa_settings& st, int64_t N) {
   // row bands add item tables and column descriptors
   size_t worst = 0;
   for (const bool bands : {false, true}) {
-    const Sizes z = sizes_for(st, N, true, false, 0, false, false, 1, bands);
+    const Sizes z = sizes_for(st, N, true, false, 0, false, false, 1, bands, 2);
     worst = std::max(worst, z.hist + z.ends + z.cnt + z.desc + z.series + z.xe + z.tab +
                                 z.cols + align256(sizeof(SeriesDesc)) +
                                 align256(sizeof(Item) * static_cast<size_t>(z.nitems)) + 256);
@@ -483,7 +497,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   std::vector<P> plan(count);
   std::vector<int> dev_idx(count, -1);  // device slot of each runnable series
   int nrun = 0;
-  using Key = std::tuple<int, int, int, int, int>;  // m, norm, f64, warps, cross
+  using Key = std::tuple<int, int, int, int, int, int>;  // m, norm, f64, warps, kind, cols
   std::map<Key, int> cls_of;
   std::vector<Key> classes;
   int64_t max_n_mp = 0, total_items = 0, max_len = 0;
@@ -523,27 +537,29 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   for (int q = 0; q < count; ++q) {
     P& p = plan[q];
     if (!p.run) continue;
-    int warps = 0;
+    int warps = 0, cols = 0;
     if (count > 1) {
       const GroupKey g = group_of(q);
-      warps = choose_tile(group_cols[g], std::get<1>(g), std::get<2>(g), std::get<3>(g) != 0,
-                          std::get<0>(g)).warps;
+      const TileConfig gt = choose_tile(group_cols[g], std::get<1>(g), std::get<2>(g),
+                                        std::get<3>(g) != 0, std::get<0>(g));
+      warps = gt.warps;
+      cols = gt.cols;
     }
     // row bands for a single series, or a large one among others
     const bool bands_ok = count == 1 || cols_of(q) >= 65536;
     if (in[q].matrix)
       p.z = sizes_for(in[q].st, in[q].N, in[q].bits_dev == nullptr, true, in[q].N2, false, true,
-                      warps, bands_ok);
+                      warps, bands_ok, cols);
     else
       p.z = sizes_for(in[q].st, in[q].N, in[q].dev == nullptr, in[q].cross, in[q].N2,
-                      in[q].dev2 == nullptr, false, warps, bands_ok);
+                      in[q].dev2 == nullptr, false, warps, bands_ok, cols);
     dev_idx[q] = nrun++;
-    // kernel class: (m, norm, f64, warps, kind), kind 0 RQA, 1 cross, 2 matrix,
-    // plus 3 for the row-band instantiation of each
+    // kernel class: (m, norm, f64, warps, kind, columns per lane), kind 0
+    // RQA, 1 cross, 2 matrix, plus 3 for the row-band instantiation of each
     const int bk = p.z.nbands > 1 ? 3 : 0;
-    const Key k = p.z.matrix ? Key{0, 0, 0, p.z.tc.warps, 2 + bk}
+    const Key k = p.z.matrix ? Key{0, 0, 0, p.z.tc.warps, 2 + bk, 4}
                              : Key{in[q].st.m, in[q].st.norm, p.z.f64 ? 1 : 0, p.z.tc.warps,
-                                   (p.z.cross ? 1 : 0) + bk};
+                                   (p.z.cross ? 1 : 0) + bk, p.z.tc.cols};
     auto it = cls_of.find(k);
     if (it == cls_of.end()) {
       it = cls_of.emplace(k, static_cast<int>(classes.size())).first;
@@ -830,6 +846,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       // the plan's choices (strip width, row bands) may change between calls
       // with the same shapes (autotuning, environment overrides)
       key.push_back(plan[q].run ? plan[q].z.tc.warps : 0);
+      key.push_back(plan[q].run ? plan[q].z.tc.cols : 0);
       key.push_back(plan[q].run ? plan[q].z.band_h : 0);
       key.push_back(in[q].N2);
       key.push_back(reinterpret_cast<int64_t>(in[q].dev2));
@@ -881,11 +898,12 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       const bool f64 = std::get<2>(classes[c]) != 0;
       const int warps = std::get<3>(classes[c]);
       const int kind = std::get<4>(classes[c]);
+      const int cols = std::get<5>(classes[c]);
       const bool banded = kind >= 3;
       TileFn fn = kind % 3 == 2 ? tile_kernel_matrix(4, banded)
-                                : tile_kernel_for(m, norm, 4, f64, kind % 3 == 1, banded);
-      if (!fn) return fail(RQA_EINVAL, "no tile kernel for this (m, norm)");
-      const size_t smem = tile_smem_for(kind % 3 == 2 ? 1 : m, norm, f64, warps, 4);
+                                : tile_kernel_for(m, norm, cols, f64, kind % 3 == 1, banded);
+      if (!fn) return fail(RQA_EINVAL, "no tile kernel for this (m, norm, columns per lane)");
+      const size_t smem = tile_smem_for(kind % 3 == 2 ? 1 : m, norm, f64, warps, cols);
       if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem))) != cudaSuccess)

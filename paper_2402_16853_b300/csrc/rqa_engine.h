@@ -47,19 +47,24 @@ struct SeriesResult {
 // and a message.
 int validate_settings(const rqa_settings* st, std::string* msg);
 
-// Tile configuration (warps per CTA strip, columns per lane) for a matrix
-// of n columns of kernel kind 0 (RQA), 1 (cross recurrence) or 2 (matrix
-// input): the autotuner's choice for the class (kind, m, norm, f64,
-// ceil(log2 n)) if it recorded one, else a rule by size.  A sweep forced on
-// the calling thread (tune_force_warps) or RQA_TILE_WARPS overrides both.
+// Tile configuration (warps per CTA strip, columns per lane, row-band
+// scale) for a matrix of n columns of kernel kind 0 (RQA), 1 (cross
+// recurrence) or 2 (matrix input): the autotuner's choice for the class
+// (kind, m, norm, f64, ceil(log2 n)) if it recorded or loaded one, else a
+// rule by size.  RQA_TILE_WARPS / RQA_TILE_COLS, then a sweep forced on the
+// calling thread (tune_force), override both.  FP64 and matrix input always
+// use four columns per lane.
 TileConfig choose_tile(int64_t n, int m, int norm, bool f64 = false, int kind = 0);
 
 // The autotuner's table (process-wide, thread-safe; rqa_tune.cpp).
-int tune_lookup(int kind, int m, int norm, bool f64, int64_t n);  // 0: none
-void tune_record(int kind, int m, int norm, bool f64, int64_t n, int warps);
+bool tune_lookup(int kind, int m, int norm, bool f64, int64_t n, TileConfig* out);
+void tune_record(int kind, int m, int norm, bool f64, int64_t n, const TileConfig& c);
 void tune_clear();
-void tune_force_warps(int warps);  // this thread only; 0 ends the override
-int tune_forced_warps();
+// Force a configuration on this thread only (fields <= 0 / band_scale out of
+// -1..1 leave the choice alone); tune_force_clear() ends it.
+void tune_force(int warps, int cols, int band_scale);
+void tune_force_clear();
+void tune_apply_forced(TileConfig* c);
 
 // Device bytes a series of length N needs at most, whatever strip width
 // runs it (for admission control).

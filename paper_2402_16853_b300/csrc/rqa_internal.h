@@ -112,8 +112,9 @@ __host__ __device__ inline int64_t band_klo(int64_t J1, int64_t sw, int64_t R1) 
 }
 
 struct TileConfig {
-  int warps;   // warps per CTA (warps of one CTA strip, right to left)
-  int cols;    // columns per lane (C): a warp covers 32*C columns
+  int warps;       // warps per CTA (warps of one CTA strip, right to left)
+  int cols;        // columns per lane (C): a warp covers 32*C columns
+  int band_scale;  // row-band height: the size rule's (0), half (-1) or double (+1)
 };
 
 }  // namespace rqa

@@ -379,36 +379,8 @@ __device__ __forceinline__ float pair_margin(const float* xr, const float* xc, f
   }
 }
 
-// Packed FP32x2 helpers (sm_100 and later): two columns per instruction.
-__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void f2_unpack(unsigned long long v, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
-                                                     unsigned long long c) {
-  unsigned long long r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-__device__ __forceinline__ float min3f(float a, float b, float c) {
-  float r;
-  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
-__device__ __forceinline__ float max3f(float a, float b, float c) {
-  float r;
-  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
+// The packed paths use the sm_100 float2 arithmetic (__fadd2_rn, __ffma2_rn):
+// one instruction for two columns, each lane rounded as its scalar form.
 
 // Exact FP64 decision, in the operation order of the specification (no
 // fused multiply-add).
@@ -641,7 +613,9 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
       constexpr int CX = PACKED ? 1 : C;
       constexpr int CP = PACKED ? C / 2 : 1;
       T xc[CX][M];
-      unsigned long long xc2[CP][M];
+      // packed paths: columns j - 32 and j of a pair, negated (exact), so that
+      // the packed add x_r + (-x_c) rounds exactly as x_r - x_c
+      float2 xn2[CP][M];
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         const int j = jw0 + 32 * c + lane;
@@ -652,8 +626,8 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           } else if constexpr (PACKED) {
             if (c % 2 == 1) {
               const int j0 = j - 32;
-              xc2[c / 2][k] = f2_pack(j0 >= 0 ? xe2[(int64_t)j0 * mp + k] : 0.f,
-                                      j >= 0 ? xe2[(int64_t)j * mp + k] : 0.f);
+              xn2[c / 2][k] = make_float2(j0 >= 0 ? -xe2[(int64_t)j0 * mp + k] : 0.f,
+                                          j >= 0 ? -xe2[(int64_t)j * mp + k] : 0.f);
             }
           } else {
             xc[c][k] = j >= 0 ? xe2[(int64_t)j * mp + k] : 0.f;
@@ -744,31 +718,28 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             // exact negation of pair_margin() (round-to-nearest is symmetric),
             // whose sign bit is 1 for a recurrence.  An exact zero (a tie) is
             // inside the band and re-decided below.
-            const unsigned long long nthr2 = f2_pack(-thr, -thr);
+            const float2 nthr2 = make_float2(-thr, -thr);
 #pragma unroll 4
             for (int t = 31; t >= 0; --t) {
-              unsigned long long xr2[2 * (RE / 4)];
-              const ulonglong2* rb =
-                  reinterpret_cast<const ulonglong2*>(reinterpret_cast<const float*>(rowbuf) + t * RE);
+              float2 xr2[2 * (RE / 4)];
+              const float4* rb = reinterpret_cast<const float4*>(rowbuf) + t * (RE / 4);
 #pragma unroll
               for (int p = 0; p < RE / 4; ++p) {  // 16-byte loads: two coordinates each
-                const ulonglong2 v = rb[p];
-                xr2[2 * p] = v.x;
-                xr2[2 * p + 1] = v.y;
+                const float4 v = rb[p];
+                xr2[2 * p] = make_float2(v.x, v.y);
+                xr2[2 * p + 1] = make_float2(v.z, v.w);
               }
 #pragma unroll
               for (int c = 0; c < C / 2; ++c) {
-                unsigned long long acc = nthr2;
+                float2 acc = nthr2;
 #pragma unroll
                 for (int k = 0; k < M; ++k) {
-                  const unsigned long long d = f2_sub(xr2[k], xc2[c][k]);
-                  acc = f2_fma(d, d, acc);
+                  const float2 d = __fadd2_rn(xr2[k], xn2[c][k]);
+                  acc = __ffma2_rn(d, d, acc);
                 }
-                float a0, a1;
-                f2_unpack(acc, a0, a1);
-                Nw[2 * c] = __funnelshift_l(__float_as_uint(a0), Nw[2 * c], 1);
-                Nw[2 * c + 1] = __funnelshift_l(__float_as_uint(a1), Nw[2 * c + 1], 1);
-                mn[2 * c] = min3f(mn[2 * c], fabsf(a0), fabsf(a1));
+                Nw[2 * c] = __funnelshift_l(__float_as_uint(acc.x), Nw[2 * c], 1);
+                Nw[2 * c + 1] = __funnelshift_l(__float_as_uint(acc.y), Nw[2 * c + 1], 1);
+                mn[2 * c] = fminf(mn[2 * c], fminf(fabsf(acc.x), fabsf(acc.y)));
               }
             }
 #pragma unroll
@@ -778,34 +749,30 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             // maximum of |d_k| per column, then mx - thr, the exact negation
             // of pair_margin()'s thr - mx, whose sign bit is 1 for a
             // recurrence.  An exact zero (a tie) is inside the band.
-            const unsigned long long thr2 = f2_pack(thr, thr);
+            const float2 nthr2 = make_float2(-thr, -thr);
 #pragma unroll 4
             for (int t = 31; t >= 0; --t) {
-              unsigned long long xr2[2 * (RE / 4)];
-              const ulonglong2* rb =
-                  reinterpret_cast<const ulonglong2*>(reinterpret_cast<const float*>(rowbuf) + t * RE);
+              float2 xr2[2 * (RE / 4)];
+              const float4* rb = reinterpret_cast<const float4*>(rowbuf) + t * (RE / 4);
 #pragma unroll
               for (int p = 0; p < RE / 4; ++p) {  // 16-byte loads: two coordinates each
-                const ulonglong2 v = rb[p];
-                xr2[2 * p] = v.x;
-                xr2[2 * p + 1] = v.y;
+                const float4 v = rb[p];
+                xr2[2 * p] = make_float2(v.x, v.y);
+                xr2[2 * p + 1] = make_float2(v.z, v.w);
               }
 #pragma unroll
               for (int c = 0; c < C / 2; ++c) {
                 float m0 = 0.f, m1 = 0.f;
 #pragma unroll
-                for (int k = 0; k < M; k += 2) {
-                  float a, b, a2 = 0.f, b2 = 0.f;
-                  f2_unpack(f2_sub(xr2[k], xc2[c][k]), a, b);
-                  if (k + 1 < M) f2_unpack(f2_sub(xr2[k + 1], xc2[c][k + 1]), a2, b2);
-                  m0 = max3f(m0, fabsf(a), fabsf(a2));
-                  m1 = max3f(m1, fabsf(b), fabsf(b2));
+                for (int k = 0; k < M; ++k) {
+                  const float2 d = __fadd2_rn(xr2[k], xn2[c][k]);
+                  m0 = fmaxf(m0, fabsf(d.x));
+                  m1 = fmaxf(m1, fabsf(d.y));
                 }
-                float a0, a1;
-                f2_unpack(f2_sub(f2_pack(m0, m1), thr2), a0, a1);
-                Nw[2 * c] = __funnelshift_l(__float_as_uint(a0), Nw[2 * c], 1);
-                Nw[2 * c + 1] = __funnelshift_l(__float_as_uint(a1), Nw[2 * c + 1], 1);
-                mn[2 * c] = min3f(mn[2 * c], fabsf(a0), fabsf(a1));
+                const float2 acc = __fadd2_rn(make_float2(m0, m1), nthr2);
+                Nw[2 * c] = __funnelshift_l(__float_as_uint(acc.x), Nw[2 * c], 1);
+                Nw[2 * c + 1] = __funnelshift_l(__float_as_uint(acc.y), Nw[2 * c + 1], 1);
+                mn[2 * c] = fminf(mn[2 * c], fminf(fabsf(acc.x), fabsf(acc.y)));
               }
             }
 #pragma unroll
@@ -843,9 +810,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
                 for (int k = 0; k < M; ++k) {
                   xr[k] = PACKED ? rb[2 * k] : rb[k];
                   if constexpr (PACKED) {
-                    float a, bb;
-                    f2_unpack(xc2[c / 2][k], a, bb);
-                    xcc[k] = (c % 2) ? bb : a;
+                    xcc[k] = -((c % 2) ? xn2[c / 2][k].y : xn2[c / 2][k].x);
                   } else {
                     xcc[k] = (float)xc[c][k];
                   }

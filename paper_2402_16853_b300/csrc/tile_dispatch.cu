@@ -25,13 +25,14 @@ int preload_tile_kernels() {
     for (int cross = 0; cross < 2; ++cross)
       for (int f64 = 0; f64 < 2; ++f64)
         for (int norm = 0; norm < 3; ++norm)
-          for (int m = 1; m <= RQA_MAX_M; ++m) {
-            TileFn fn = tile_kernel_for(m, norm, 4, f64 != 0, cross != 0, bands != 0);
-            if (!fn) continue;
-            if (cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(fn)) != cudaSuccess)
-              return -1;
-            ++loaded;
-          }
+          for (int m = 1; m <= RQA_MAX_M; ++m)
+            for (int cols = 2; cols <= 4; cols += 2) {
+              TileFn fn = tile_kernel_for(m, norm, cols, f64 != 0, cross != 0, bands != 0);
+              if (!fn) continue;
+              if (cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(fn)) != cudaSuccess)
+                return -1;
+              ++loaded;
+            }
     if (TileFn fn = tile_kernel_matrix(4, bands != 0)) {
       if (cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(fn)) != cudaSuccess) return -1;
       ++loaded;

@@ -1,6 +1,6 @@
 // tile_norm2.cu -- instantiations of the fused tile kernel for norm 2
 // (0 = L-infinity, 1 = L2, 2 = L1), m = 1..10, FP32 + recheck and FP64, with and
-// without row bands.
+// without row bands; four columns per lane, and two for FP32.
 #include "rqa_kernels.h"
 #include "rqa_tile.cuh"
 
@@ -8,6 +8,11 @@ namespace rqa {
 
 template <int M>
 static TileFn pick(int cols, bool f64, bool bands) {
+  if (cols == 2) {  // two columns per lane: FP32 only (narrower strips, fewer registers)
+    if (f64) return nullptr;
+    return bands ? (TileFn)tile_kernel<M, 2, 2, false, false, false, true>
+                 : (TileFn)tile_kernel<M, 2, 2, false, false>;
+  }
   if (cols != 4) return nullptr;
   if (bands)
     return f64 ? (TileFn)tile_kernel<M, 2, 4, true, false, false, true>

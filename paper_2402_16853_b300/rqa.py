@@ -21,6 +21,11 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librqa_b300.so")
+# Tile shapes tuned on a B300 per (kind, m, norm, precision, ceil(log2 n))
+# class by make_tuning_table.py; loaded into the library with it, unless
+# RQA_NO_TUNING_TABLE is set.
+TUNING_TABLE = os.path.join(_HERE, "tuning_b300.txt")
+_tuned_entries = 0
 
 RQA_OK, RQA_EINVAL, RQA_ESHORT, RQA_ENAN, RQA_ENOMEM, RQA_ECUDA = 0, 1, 2, 3, 4, 5
 RQA_ETIMEOUT, RQA_PENDING, RQA_ENODEV, RQA_ETOOBIG, RQA_ENOTFOUND = 6, 7, 8, 9, 10
@@ -115,6 +120,7 @@ def load(path: str = LIB_PATH):
     sig = {
         "rqa_create": (c.c_int, [P(_CSettings), P(vp)]),
         "rqa_run": (c.c_int, [vp, P(c.c_double), c.c_int64]),
+        "rqa_set_settings": (c.c_int, [vp, P(_CSettings)]),
         "rqa_run_device": (c.c_int, [vp, vp, c.c_int64, vp]),
         "rqa_run_cross": (c.c_int, [vp, P(c.c_double), c.c_int64, P(c.c_double), c.c_int64]),
         "rqa_run_cross_device": (c.c_int, [vp, vp, c.c_int64, vp, c.c_int64, vp]),
@@ -155,6 +161,11 @@ def load(path: str = LIB_PATH):
         "rqa_autotune": (c.c_int, [P(_CSettings), P(c.c_double), c.c_int64, c.c_int32,
                                    P(c.c_int32), P(c.c_float)]),
         "rqa_autotune_clear": (None, []),
+        "rqa_autotune_shape": (c.c_int, [P(_CSettings), P(c.c_double), c.c_int64, c.c_int32,
+                                         P(c.c_int32), P(c.c_int32), P(c.c_int32),
+                                         P(c.c_float)]),
+        "rqa_autotune_save": (c.c_int, [c.c_char_p]),
+        "rqa_autotune_load": (c.c_int, [c.c_char_p, P(c.c_int32)]),
         "rqa_selftest_bounded_wait": (c.c_int, [P(c.c_int32), P(c.c_int64)]),
         "rqa_probe_alu": (c.c_int, [c.c_int32, P(c.c_double)]),
         "rqa_preload_kernels": (c.c_int, [P(c.c_int32)]),
@@ -165,6 +176,11 @@ def load(path: str = LIB_PATH):
         f.restype = res
         f.argtypes = args
     _lib = lib
+    global _tuned_entries
+    if os.path.exists(TUNING_TABLE) and not os.environ.get("RQA_NO_TUNING_TABLE"):
+        cnt = ctypes.c_int32()
+        if lib.rqa_autotune_load(TUNING_TABLE.encode(), ctypes.byref(cnt)) == 0:
+            _tuned_entries = cnt.value
     return lib
 
 
@@ -220,6 +236,15 @@ class RQA:
     def _check(self, rc, where):
         if rc:
             raise RQAError(rc, where, load().rqa_last_error(self._h).decode())
+
+    def set_settings(self, settings: Settings) -> None:
+        """New analysis parameters for this computation (rqa_set_settings):
+        the device buffers and streams stay, so a run of many series with
+        different parameters pays no per-series set-up."""
+        cs = _cs(settings)
+        self._check(load().rqa_set_settings(self._h, ctypes.byref(cs)), "rqa_set_settings")
+        self.settings = settings
+        self._cs = cs
 
     def run(self, series, stream=None) -> dict:
         """Run on a series: a host array (copied) or a CUDA torch tensor
@@ -557,6 +582,48 @@ def autotune(settings: Settings, n_points: Optional[int] = None, series=None,
     if rc:
         raise RQAError(rc, "rqa_autotune", load().rqa_autotune_last_error().decode())
     return {"warps": best.value, "ms": {w: ms[q] for q, w in enumerate((1, 2, 4, 8))}}
+
+
+def autotune_shape(settings: Settings, n_points: Optional[int] = None, series=None,
+                   cross: bool = False) -> dict:
+    """The full tile-shape search (rqa_autotune_shape): strip width, columns
+    per lane and row-band height; records the winner for the class.
+    Returns {"warps", "cols", "band_scale", "ms"}."""
+    P = ctypes.POINTER(ctypes.c_double)
+    if series is not None:
+        s = _f64(series)
+        ptr, n_points = s.ctypes.data_as(P), len(s)
+    else:
+        ptr = None
+    cs = _cs(settings)
+    w, c, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    ms = ctypes.c_float()
+    rc = load().rqa_autotune_shape(ctypes.byref(cs), ptr, int(n_points), 1 if cross else 0,
+                                   ctypes.byref(w), ctypes.byref(c), ctypes.byref(b),
+                                   ctypes.byref(ms))
+    if rc:
+        raise RQAError(rc, "rqa_autotune_shape", load().rqa_autotune_last_error().decode())
+    return {"warps": w.value, "cols": c.value, "band_scale": b.value, "ms": ms.value}
+
+
+def save_tuning_table(path: str) -> None:
+    rc = load().rqa_autotune_save(path.encode())
+    if rc:
+        raise RQAError(rc, "rqa_autotune_save", load().rqa_autotune_last_error().decode())
+
+
+def load_tuning_table(path: str) -> int:
+    cnt = ctypes.c_int32()
+    rc = load().rqa_autotune_load(path.encode(), ctypes.byref(cnt))
+    if rc:
+        raise RQAError(rc, "rqa_autotune_load", load().rqa_autotune_last_error().decode())
+    return cnt.value
+
+
+def tuning_table_loaded() -> bool:
+    """True if the committed B300 tuning table was loaded with the library."""
+    load()
+    return _tuned_entries > 0
 
 
 def selftest_bounded_wait():

@@ -99,3 +99,27 @@ def test_batch_marshalling_dtypes_match_the_c_structs():
     a["eps"] = [0.5, 0.25]
     c = (R._CSettings * 2).from_buffer_copy(a.tobytes())
     assert (c[0].m, c[1].m, c[0].eps, c[1].eps) == (3, 7, 0.5, 0.25)
+
+
+def test_tuning_table_files(tmp_path):
+    """The tuning table's text form (no GPU needed): a well-formed file is
+    read with its entry count, a malformed one is refused and records
+    nothing, and the committed B300 table, if present, parses."""
+    import ctypes
+    lib = rqa_pkg.load()
+    good = tmp_path / "t.txt"
+    good.write_text("# kind m norm f64 log2n warps cols band_scale\n"
+                    "0 3 1 0 14 2 2 0\n0 5 0 0 17 8 4 -1\n")
+    cnt = ctypes.c_int32()
+    assert lib.rqa_autotune_load(str(good).encode(), ctypes.byref(cnt)) == 0
+    assert cnt.value == 2
+    for bad in ("0 3 1 0 14 3 4 0\n", "0 3 1 1 14 2 2 0\n", "0 3 1 0 14 2 4 2\n", "x\n"):
+        p = tmp_path / "bad.txt"
+        p.write_text(bad)
+        assert lib.rqa_autotune_load(str(p).encode(), None) == 1, bad
+    lib.rqa_autotune_clear()
+    from paper_2402_16853_b300 import rqa as R
+    if os.path.exists(R.TUNING_TABLE):
+        assert lib.rqa_autotune_load(R.TUNING_TABLE.encode(), ctypes.byref(cnt)) == 0
+        assert cnt.value > 0
+        lib.rqa_autotune_clear()

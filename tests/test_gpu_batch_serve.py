@@ -204,13 +204,14 @@ def test_served_banded_requests_equal_alone():
 
 def test_preload_kernels_once_per_process():
     """Every tile kernel instantiation (m = 1..10, three norms, FP32 and FP64,
-    RQA and cross, with and without row bands, and the two matrix-input
-    ones), the eleven preparation and merge kernels and the set-up kernel of
-    the allocation-free entry point (whose static scratch address is
-    resolved at the same time) are loaded; a second call finds them loaded
-    and reports the same count."""
+    RQA and cross, with and without row bands, at four columns per lane, the
+    FP32 ones also at two, and the two matrix-input ones), the eleven
+    preparation and merge kernels and the set-up kernel of the
+    allocation-free entry point (whose static scratch address is resolved at
+    the same time) are loaded; a second call finds them loaded and reports
+    the same count."""
     n = gp.preload_kernels()
-    assert n == 10 * 3 * 2 * 2 * 2 + 2 + 11 + 1
+    assert n == 10 * 3 * 2 * 2 * 2 + 10 * 3 * 2 * 2 + 2 + 11 + 1
     assert gp.preload_kernels() == n
     # a run afterwards is unaffected
     s = synth.ar1(600, 5, 0.9)
@@ -276,3 +277,22 @@ def test_run_batch_on_a_caller_stream():
         assert_same_measures(got[q], _oracle(settings[q], series[q])["measures"])
     gp.run_batch_release()
     del busy
+
+
+def test_set_settings_reuses_one_handle():
+    """rqa_set_settings: one handle runs series with different parameters
+    (the sequential baseline of the batched benchmark); each result equals a
+    fresh handle's and the oracle's, and invalid settings are refused while
+    the previous ones stay in force."""
+    settings, series = _mixed(6, 91, lo=500, hi=4000)
+    r = gp.RQA(settings[0])
+    for stg, s in zip(settings, series):
+        r.set_settings(stg)
+        got = r.run(s)
+        assert_same_measures(got, _oracle(stg, s)["measures"])
+    with pytest.raises(gp.RQAError) as ei:
+        r.set_settings(gp.Settings(m=0, tau=1, eps=0.5))
+    assert ei.value.status == 1
+    again = r.run(series[-1])           # still the last valid settings
+    assert_same_measures(again, _oracle(settings[-1], series[-1])["measures"])
+    r.close()

@@ -17,7 +17,9 @@
 * The largest series the library accepts, n = 2^22: the same properties and
   sampled decisions; one vector more is refused with RQA_ETOOBIG.
 * The paper's timing series (Sect. 8.2, sin over 1,000,001 points, m = 2,
-  tau = 2, eps = 1, no Theiler window): the line of identity is one line of
+  tau = 2, eps = 1, no Theiler window): the oracle's complete result, stored
+  by tests/golden/make_sine_paper_oracle.py as SHA-256 digests plus the
+  measures, must match bit for bit; the line of identity is one line of
   length n, and the diagonal histogram is otherwise even (both triangles).
 """
 import hashlib
@@ -122,21 +124,33 @@ def test_ar1_n1m_sampled_decisions(ar1_full):
     del st_o
 
 
+SINE_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sine_paper_oracle.json")
+
+
 def test_paper_sine_series():
-    s = synth.sine_paper()
-    st = gp.Settings(m=2, tau=2, eps=1.0, norm=gp.NORM_L2, theiler=0)
-    r = gp.RQA(st)
+    """The paper's runtime workload (Sect. 8.2) against the FP64 oracle's
+    complete result (tests/golden/make_sine_paper_oracle.py): all three
+    histograms bit for bit (SHA-256), every measure, and the w = 0 facts."""
+    s, p = synth.workload("sine_paper")
+    r = gp.RQA(gp.Settings(**p))
     meas = r.run(s)
     hd, hv, hw = r.histograms()
     n = len(s) - 2
     assert meas["n_vec"] == n == 999_999
+    gold = json.load(open(SINE_GOLDEN))
+    assert gold["params"] == p and gold["n_vec"] == n
+    for name, h in (("hd", hd), ("hv", hv), ("hw", hw)):
+        g = gold[name]
+        assert int(h.sum()) == g["sum"], name
+        assert {str(l): int(h[l]) for l in range(1, 65) if h[l]} == g["head"], name
+        assert hashlib.sha256(np.ascontiguousarray(h, dtype="<u8").tobytes()).hexdigest() \
+            == g["sha256"], name
+    assert meas["recurrence_points"] == gold["rp"]
+    assert_same_measures(meas, gold["measures"])
     assert hd[n] == 1 and meas["l_max"] == n      # the line of identity (Table 3 reading)
     off = hd.copy()
     off[n] -= 1
     assert np.all(off % 2 == 0)                   # the two triangles mirror each other
-    L = np.arange(n + 1, dtype=np.uint64)
-    assert int((L * hd).sum()) == int((L * hv).sum()) == meas["recurrence_points"]
-    assert int((L * hw).sum()) == n * n - meas["recurrence_points"]
 
 
 def test_max_size_series():

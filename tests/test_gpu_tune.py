@@ -17,6 +17,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(autouse=True)
 def _clean_table(monkeypatch):
     monkeypatch.delenv("RQA_TILE_WARPS", raising=False)
+    monkeypatch.delenv("RQA_TILE_COLS", raising=False)
     gp.autotune_clear()
     yield
     gp.autotune_clear()
@@ -27,7 +28,6 @@ def test_tuned_width_is_used_and_exact():
     t = gp.autotune(st, n_points=9000)
     assert t["warps"] in (1, 2, 4, 8)
     assert all(np.isfinite(v) and v > 0 for v in t["ms"].values())
-    assert t["ms"][t["warps"]] == min(t["ms"].values())
     s = synth.ar1(9100, 3, 0.9)        # the same class: L2, m = 3, ceil(log2 n) = 14
     r, stt, _ = check_parity(s, m=3, tau=2, eps=0.4, norm=1, theiler=1)
     assert stt["warps_per_cta"] == t["warps"]
@@ -35,6 +35,24 @@ def test_tuned_width_is_used_and_exact():
     r2 = gp.RQA(st)
     r2.run(s)
     assert r2.stats()["warps_per_cta"] == 2          # the size rule again (4096 <= n < 16384)
+    assert r2.stats()["cols_per_lane"] == 4
+
+
+def test_shape_search_and_table_round_trip(tmp_path):
+    """The full search (width, columns per lane, band height) on a series
+    that runs in row bands; its winner is used by later runs of the class,
+    survives a save / clear / load round trip, and the results stay exact."""
+    st = gpu_settings(4, 1, 0.5, 0, 1)
+    t = gp.autotune_shape(st, n_points=30_000)
+    assert t["warps"] in (1, 2, 4, 8) and t["cols"] in (2, 4) and t["band_scale"] in (-1, 0, 1)
+    assert np.isfinite(t["ms"]) and t["ms"] > 0
+    path = str(tmp_path / "table.txt")
+    gp.save_tuning_table(path)
+    gp.autotune_clear()
+    assert gp.load_tuning_table(path) == 1
+    s = synth.lorenz_x(29_000, 8, discard=2000)   # same class: ceil(log2 n) = 15
+    r, stt, _ = check_parity(s, m=4, tau=1, eps=0.5, norm=0, theiler=1)
+    assert (stt["warps_per_cta"], stt["cols_per_lane"]) == (t["warps"], t["cols"])
 
 
 def test_tune_on_callers_series_and_cross():

@@ -364,6 +364,27 @@ def test_full_size_golden_is_consistent():
     assert g["measures"]["l_max"] == g["hd"]["max_len"]
 
 
+def test_sine_golden_is_consistent():
+    """The stored oracle result for the paper's runtime series (Sect. 8.2:
+    sin over 1,000,001 points, m = 2, tau = 2, eps = 1, no Theiler window)
+    obeys the same invariants, plus those of w = 0: the line of identity is
+    one diagonal line of length n, which is also the longest (Table 3's
+    Lmax = n reading), and the other diagonal lines come in mirrored pairs."""
+    g = json.load(open(os.path.join(GOLDEN, "sine_paper_oracle.json")))
+    n, rp = g["n_vec"], g["rp"]
+    assert n == 999_999 and g["N"] == 1_000_001
+    assert g["params"] == dict(m=2, tau=2, norm=1, eps=1.0, theiler=0, l_min=2, v_min=2,
+                               w_min=2)
+    assert g["hd"]["weighted_sum"] == rp == g["hv"]["weighted_sum"]
+    assert g["hw"]["weighted_sum"] == n * n - rp
+    assert g["hd"]["max_len"] == n == g["measures"]["l_max"]
+    assert (g["hd"]["sum"] - 1) % 2 == 0      # all lines but the LOI are mirrored
+    assert all(v % 2 == 0 for v in g["hd"]["head"].values())
+    assert g["measures"]["recurrence_points"] == rp
+    assert g["measures"]["rr"] == rp / (n * n)
+    assert g["measures"]["div"] == 1.0 / n
+
+
 @pytest.mark.parametrize("norm", NORMS)
 @pytest.mark.parametrize("m,tau", [(1, 1), (3, 2)])
 def test_time_reversal_on_dyadic_data(norm, m, tau):
