@@ -534,6 +534,23 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
         int64_t& g = group_cols[group_of(q)];
         g = std::max(g, cols_of(q));
       }
+  // Row bands in a set of several series: a series is cut into bands when
+  // its tallest strip (rows / 32 block rows for one CTA) would outlast the
+  // set's balanced share per resident CTA, i.e. when it alone would form
+  // the launch's tail.  The set's work is counted in block rows of
+  // 1,024-column strips (a rows x cols series: cols/1024 strips, rows/64
+  // block rows on average for a triangle, rows/32 for a rectangle).
+  double set_block_rows = 0.0;
+  if (count > 1)
+    for (int q = 0; q < count; ++q)
+      if (plan[q].run) {
+        const double rows =
+            static_cast<double>(in[q].matrix ? in[q].N : nvec_of(in[q].st, in[q].N));
+        const double cols = static_cast<double>(cols_of(q));
+        const double per_strip = rows / ((in[q].cross || in[q].matrix) ? 32.0 : 64.0);
+        set_block_rows += (cols / 1024.0 + 1.0) * per_strip;
+      }
+  const double share = set_block_rows / (3.0 * sms_);
   for (int q = 0; q < count; ++q) {
     P& p = plan[q];
     if (!p.run) continue;
@@ -545,8 +562,10 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       warps = gt.warps;
       cols = gt.cols;
     }
-    // row bands for a single series, or a large one among others
-    const bool bands_ok = count == 1 || cols_of(q) >= 65536;
+    // row bands for a single series, or for one that would be the set's tail
+    const double rows_q =
+        static_cast<double>(in[q].matrix ? in[q].N : nvec_of(in[q].st, in[q].N));
+    const bool bands_ok = count == 1 || rows_q / 32.0 > share;
     if (in[q].matrix)
       p.z = sizes_for(in[q].st, in[q].N, in[q].bits_dev == nullptr, true, in[q].N2, false, true,
                       warps, bands_ok, cols);

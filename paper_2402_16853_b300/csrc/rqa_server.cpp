@@ -9,8 +9,7 @@
 // admitted series in one submission), and publish the results.  An epoch
 // formed from requests that arrived while other epochs run goes to the
 // device at once on its worker's streams, so work of different epochs
-// overlaps; with sixteen workers a burst of large requests rarely leaves a
-// small one waiting for a free worker.  Per-request histograms and boundary
+// overlaps, while four workers keep the number of epochs sharing the GPU low.  Per-request histograms and boundary
 // state live in the epoch's device arena until the epoch completes.
 #include <chrono>
 #include <cstdlib>
@@ -46,7 +45,7 @@ struct Request {
 struct rqa_server {
   size_t budget = 0;
   int32_t max_slots = 0;
-  int workers_n = 16;
+  int workers_n = 4;
   // An epoch stops admitting once it holds this many matrix cells (about 10 ms
   // of tile-kernel work), so epochs stay short and a request that arrives
   // while one runs is picked up by the next free worker.
@@ -147,7 +146,10 @@ int rqa_server_create(size_t mem_budget_bytes, int32_t max_slots, rqa_server** o
   s->budget = mem_budget_bytes;
   s->max_slots = max_slots;
   s->device = dev;
-  s->workers_n = 16;  // measured: p99 46-49 ms against 54-60 ms with four
+  // measured on the served mix (8 s Poisson streams): four workers keep p99
+  // at 46 ms at 200 req/s and 129 ms at 400 req/s (sixteen: 57 and 313 ms,
+  // their epochs sharing the GPU) and serve the most at 600 req/s (491/s)
+  s->workers_n = 4;
   if (const char* e = std::getenv("RQA_SERVE_WORKERS")) {  // tuning override
     const int w = std::atoi(e);
     if (w >= 1 && w <= 32) s->workers_n = w;
