@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--no-matrix", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--no-saturation", action="store_true",
-                    help="skip the served-rate sweep (16 workers vs one sequential worker)")
+                    help="skip the served-rate sweep (the server vs one sequential worker)")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--N", type=int, default=0,
                     help="series length override (default: the 1,048,576-point workload)")

@@ -350,6 +350,20 @@ const char* rqa_autotune_last_error(void);
  * the SM cycles it waited.  Returns RQA_OK if the wait gave up and raised the
  * abort flag; the CUDA context stays usable afterwards. */
 int rqa_selftest_bounded_wait(int32_t* status, int64_t* cycles_waited);
+/* The same mechanism inside the real tile kernel: runs the handle's series
+ * (host_series, n_points values; the handle's settings must be m = 3, L2,
+ * FP32 distances) through a test instantiation of the tile kernel with eight
+ * warps per CTA strip, no row bands and a wait limit of 10^6 SM cycles, in
+ * which warp `warp` (0..6) of every CTA stops handing its row and diagonal
+ * carries to warp `warp` + 1 from its `from_handover`-th hand-over (>= 1)
+ * on.  The waiting warp gives up, raises the CTA's abort flag (every other
+ * wait of the CTA then returns), and the series fails: the call returns
+ * RQA_ETIMEOUT if the strips reach that hand-over (a series too short to
+ * reach it returns RQA_OK).  No wait is unbounded and nothing faults; the
+ * handle stays usable, and its next run is exact. */
+int rqa_selftest_ring_timeout(rqa_handle* h, const double* host_series,
+                              int64_t n_points, int32_t warp,
+                              int32_t from_handover);
 /* ---------------------------------------------------------- ALU probe
  * The paper has no counterpart.  rqa_probe_alu() measures, on the current
  * device, the throughput of one FP32 operation of the distance loop with

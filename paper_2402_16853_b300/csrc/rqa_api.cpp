@@ -281,6 +281,38 @@ int rqa_preload_kernels(int32_t* loaded) {
   return RQA_OK;
 }
 
+int rqa_selftest_ring_timeout(rqa_handle* h, const double* host_series, int64_t n_points,
+                              int32_t warp, int32_t from_handover) {
+  if (!h || !host_series) return RQA_EINVAL;
+  if (h->st.m != 3 || h->st.norm != RQA_NORM_L2 || h->st.precision == RQA_PREC_FP64) {
+    h->err = "the ring-timeout self-test runs m = 3, L2, FP32 distances";
+    return RQA_EINVAL;
+  }
+  if (warp < 0 || warp > 6 || from_handover < 1) {
+    h->err = "warp must be 0..6 (it needs a right neighbour's consumer) and the hand-over >= 1";
+    return RQA_EINVAL;
+  }
+  h->have = false;
+  h->err.clear();
+  std::vector<rqa::SeriesInput> in(1);
+  in[0].st = h->st;
+  in[0].host = host_series;
+  in[0].N = n_points;
+  in[0].withhold_warp = warp + 1;
+  in[0].withhold_seq = from_handover;
+  rqa::tune_force(8, 4, 0);  // eight warps per strip, so the warp has a consumer
+  std::vector<rqa::SeriesResult> res;
+  const int rc = h->eng->run(in, res, nullptr, false);
+  rqa::tune_force_clear();
+  if (rc != RQA_OK) {
+    h->err = h->eng->error();
+    return rc;
+  }
+  h->res = std::move(res[0]);  // the withheld hand-over was never reached
+  h->have = true;
+  return RQA_OK;
+}
+
 int rqa_selftest_bounded_wait(int32_t* status, int64_t* cycles_waited) {
   std::string msg;
   int dev = 0;

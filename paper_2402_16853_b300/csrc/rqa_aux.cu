@@ -71,7 +71,7 @@ __global__ void prepare_scan_kernel(SeriesDesc* __restrict__ sd) {
     mx = fmax(mx, s_mx[w]);
     bad |= s_bad[w];
   }
-  if (bad) atomicExch(&S.counters[CNT_STATUS], 3ull /* RQA_ENAN */);
+  if (bad) atomicCAS(&S.counters[CNT_STATUS], 0ull, 3ull /* RQA_ENAN */);
   if (mn <= mx) {  // the block saw a finite value
     atomicMax(&S.counters[CNT_LO], ~ordered_bits(mn));
     atomicMax(&S.counters[CNT_HI], ordered_bits(mx));
@@ -178,7 +178,7 @@ struct BlockHist {
     else if (len > 0 && len <= (uint64_t)S.hl)
       atomicAdd(&S.hist[type * (S.hl + 1) + len], 1ull);
     else
-      atomicExch(&S.counters[CNT_STATUS], STATUS_INTERNAL);
+      atomicCAS(&S.counters[CNT_STATUS], 0ull, STATUS_INTERNAL);  // the first error stays
   }
   __device__ void flush(const SeriesDesc& S) {
     __syncthreads();

@@ -497,7 +497,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   std::vector<P> plan(count);
   std::vector<int> dev_idx(count, -1);  // device slot of each runnable series
   int nrun = 0;
-  using Key = std::tuple<int, int, int, int, int, int>;  // m, norm, f64, warps, kind, cols
+  // m, norm, f64, warps, kind, cols, wait test
+  using Key = std::tuple<int, int, int, int, int, int, int>;
   std::map<Key, int> cls_of;
   std::vector<Key> classes;
   int64_t max_n_mp = 0, total_items = 0, max_len = 0;
@@ -565,7 +566,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     // row bands for a single series, or for one that would be the set's tail
     const double rows_q =
         static_cast<double>(in[q].matrix ? in[q].N : nvec_of(in[q].st, in[q].N));
-    const bool bands_ok = count == 1 || rows_q / 32.0 > share;
+    const bool bands_ok = in[q].withhold_warp == 0 && (count == 1 || rows_q / 32.0 > share);
     if (in[q].matrix)
       p.z = sizes_for(in[q].st, in[q].N, in[q].bits_dev == nullptr, true, in[q].N2, false, true,
                       warps, bands_ok, cols);
@@ -576,9 +577,10 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     // kernel class: (m, norm, f64, warps, kind, columns per lane), kind 0
     // RQA, 1 cross, 2 matrix, plus 3 for the row-band instantiation of each
     const int bk = p.z.nbands > 1 ? 3 : 0;
-    const Key k = p.z.matrix ? Key{0, 0, 0, p.z.tc.warps, 2 + bk, 4}
+    const int wt = in[q].withhold_warp > 0 ? 1 : 0;
+    const Key k = p.z.matrix ? Key{0, 0, 0, p.z.tc.warps, 2 + bk, 4, 0}
                              : Key{in[q].st.m, in[q].st.norm, p.z.f64 ? 1 : 0, p.z.tc.warps,
-                                   (p.z.cross ? 1 : 0) + bk, p.z.tc.cols};
+                                   (p.z.cross ? 1 : 0) + bk, p.z.tc.cols, wt};
     auto it = cls_of.find(k);
     if (it == cls_of.end()) {
       it = cls_of.emplace(k, static_cast<int>(classes.size())).first;
@@ -749,6 +751,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     }
     d.xe = (p.z.f64 || p.z.matrix) ? nullptr : reinterpret_cast<float*>(arena_ + p.o_xe);
     d.N = in[q].N;
+    d.withhold_warp = in[q].withhold_warp;
+    d.withhold_seq = in[q].withhold_seq;
     d.n = p.z.n;
     desc_set_symmetric(d);
     if (p.z.matrix) {
@@ -921,6 +925,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       const bool banded = kind >= 3;
       TileFn fn = kind % 3 == 2 ? tile_kernel_matrix(4, banded)
                                 : tile_kernel_for(m, norm, cols, f64, kind % 3 == 1, banded);
+      if (std::get<6>(classes[c])) fn = tile_kernel_wait_test();
       if (!fn) return fail(RQA_EINVAL, "no tile kernel for this (m, norm, columns per lane)");
       const size_t smem = tile_smem_for(kind % 3 == 2 ? 1 : m, norm, f64, warps, cols);
       if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),

@@ -29,6 +29,10 @@ struct SeriesInput {
   bool matrix = false;
   const uint32_t* bits_host = nullptr;
   const uint32_t* bits_dev = nullptr;
+  // self-test of the bounded ring waits (rqa_selftest_ring_timeout): run
+  // the tile kernel's test instantiation with warp withhold_warp - 1
+  // withholding its hand-overs from the withhold_seq-th on (0: off)
+  int32_t withhold_warp = 0, withhold_seq = 0;
 };
 
 struct SeriesResult {

@@ -51,6 +51,12 @@ struct SeriesDesc {
   uint32_t* colend;           // [n] run of column j touching row j-1
   uint32_t* rowend;           // [n] run of row i touching column i+1
   unsigned long long* counters;  // [0] rechecks, [1] status (rqa_status)
+  // ---- test of the bounded ring waits (read only by the test instantiation
+  // of the tile kernel; 0 = off): warp withhold_warp - 1 of every CTA stops
+  // publishing its carries from its withhold_seq-th hand-over on, so the
+  // next warp's wait must give up
+  int32_t withhold_warp;
+  int32_t withhold_seq;
 };
 
 // Fill the column-series fields of an RQA (symmetric) descriptor: the

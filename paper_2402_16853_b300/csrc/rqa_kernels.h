@@ -22,6 +22,9 @@ TileFn tile_kernel_norm2(int m, int cols, bool f64, bool bands);
 TileFn tile_kernel_cross_norm0(int m, int cols, bool f64, bool bands);
 TileFn tile_kernel_cross_norm1(int m, int cols, bool f64, bool bands);
 TileFn tile_kernel_cross_norm2(int m, int cols, bool f64, bool bands);
+// The test instantiation of the bounded ring waits: m = 3, L2, four
+// columns per lane, FP32 + recheck, RQA, no row bands, a short wait limit.
+TileFn tile_kernel_wait_test();
 // Line detection over a precomputed bit matrix (no distances).
 TileFn tile_kernel_matrix(int cols, bool bands = false);
 

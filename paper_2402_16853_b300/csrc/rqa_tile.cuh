@@ -53,6 +53,9 @@ constexpr uint32_t FULL = 0xffffffffu;
 constexpr int HB = 1024;     // shared-memory histogram bins per line type
 constexpr int RING = 8;      // slots of the warp-to-warp carry ring
 constexpr long long SPIN_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+// The test instantiation's limit (~0.5 ms): its test withholds a hand-over
+// on purpose, so the wait must give up quickly; far above a block's time.
+constexpr long long TEST_SPIN_CYCLES = 1000000LL;
 
 // Run state words.  Two-colour state (rows, columns): length in bits 0..27,
 // colour in bit 28, flag in bit 29 (the run touches the strip's right edge
@@ -176,9 +179,9 @@ struct HistSink {
       if (len > 0 && len <= n)
         atomicAdd(&gl[(size_t)type * (n + 1) + len], 1ull);
       else
-        atomicExch(status, STATUS_INTERNAL);
+        atomicCAS(status, 0ull, STATUS_INTERNAL);  // the first error stays
     }
-    if (cnt > (uint32_t)OVF && lane == 0) atomicExch(status, STATUS_INTERNAL);
+    if (cnt > (uint32_t)OVF && lane == 0) atomicCAS(status, 0ull, STATUS_INTERNAL);
     __syncwarp();
     if (lane == 0) *q = 0;
     __syncwarp();
@@ -449,11 +452,12 @@ __device__ __forceinline__ bool exact_decision_regs(const double* xr, const doub
 // Bounded spin on a shared-memory counter.  Returns false (and raises the
 // CTA abort flag) if the wait gave up or another warp already aborted.
 __device__ __forceinline__ bool spin_until_ge(volatile int* ctr, int target,
-                                              volatile int* abort_flag) {
+                                              volatile int* abort_flag,
+                                              long long limit = SPIN_CYCLES) {
   const long long t0 = clock64();
   while (*ctr < target) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > SPIN_CYCLES) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       return false;
     }
@@ -493,10 +497,14 @@ inline size_t tile_smem_bytes(int warps, int row_elems, int elem_bytes, int cols
 }
 
 // ------------------------------------------------------------------ kernel
-template <int M, int NORM, int C, bool F64, bool XR, bool MX = false, bool BD = false>
+// TW: the test instantiation of the bounded waits (TEST_SPIN_CYCLES, and
+// the series' withhold_warp / withhold_seq honoured).
+template <int M, int NORM, int C, bool F64, bool XR, bool MX = false, bool BD = false,
+          bool TW = false>
 __global__ void __launch_bounds__(256, 3)
 tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, int nitems,
             int* __restrict__ queue) {
+  constexpr long long spin_limit = TW ? TEST_SPIN_CYCLES : SPIN_CYCLES;
   using T = typename std::conditional<F64, double, float>::type;
   constexpr int RE = tile_row_elems<M, NORM, F64>();
   constexpr bool PACKED = !F64 && NORM != 2 && (C % 2 == 0);  // L2 and L-infinity
@@ -859,7 +867,8 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           rst = ST_FLAG;
           dL = DG_EDGE;
         } else {
-          if (lane == 0) ok = spin_until_ge(prod + (warp - 1), seq_in + 1, &s_abort);
+          if (lane == 0)
+            ok = spin_until_ge(prod + (warp - 1), seq_in + 1, &s_abort, spin_limit);
           ok = __shfl_sync(FULL, ok, 0);
           if (!ok) break;
           __threadfence_block();
@@ -995,7 +1004,8 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           if (kx >= klo)
             dia_z[off + kx - klo] = (uint16_t)((dL & ST_LEN) | ((dL & DG_EDGE) ? 0x8000u : 0u));
         } else if (b <= bhi_left) {
-          if (lane == 0) ok = spin_until_ge(cons + (warp + 1), seq_out - RING + 1, &s_abort);
+          if (lane == 0)
+            ok = spin_until_ge(cons + (warp + 1), seq_out - RING + 1, &s_abort, spin_limit);
           ok = __shfl_sync(FULL, ok, 0);
           if (!ok) break;
           uint32_t* slot = ring_out + (seq_out % RING) * 64;
@@ -1003,7 +1013,11 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           slot[32 + lane] = dL;
           __syncwarp();
           __threadfence_block();
-          if (lane == 0) prod[warp] = seq_out + 1;
+          // test instantiation: from the chosen hand-over on, this warp stops
+          // publishing, and the next warp's bounded wait gives up
+          const bool withhold =
+              TW && warp + 1 == Sp->withhold_warp && seq_out + 1 >= Sp->withhold_seq;
+          if (lane == 0 && !withhold) prod[warp] = seq_out + 1;
           ++seq_out;
         }
       }
@@ -1042,7 +1056,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
     }
     __syncthreads();
     if (s_abort && threadIdx.x == 0)
-      atomicExch(&Sp->counters[CNT_STATUS], 6ull /* RQA_ETIMEOUT */);
+      atomicCAS(&Sp->counters[CNT_STATUS], 0ull, 6ull /* RQA_ETIMEOUT */);
     // flush the strip's histograms
     const int64_t stride = (int64_t)(XR ? (int)Sp->hl : n) + 1;
     for (int q = threadIdx.x; q < 3 * HB; q += blockDim.x) {

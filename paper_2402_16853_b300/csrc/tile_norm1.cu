@@ -37,4 +37,8 @@ TileFn tile_kernel_norm1(int m, int cols, bool f64, bool bands) {
   }
 }
 
+TileFn tile_kernel_wait_test() {
+  return (TileFn)tile_kernel<3, 1, 4, false, false, false, false, true>;
+}
+
 }  // namespace rqa

@@ -167,6 +167,8 @@ def load(path: str = LIB_PATH):
         "rqa_autotune_save": (c.c_int, [c.c_char_p]),
         "rqa_autotune_load": (c.c_int, [c.c_char_p, P(c.c_int32)]),
         "rqa_selftest_bounded_wait": (c.c_int, [P(c.c_int32), P(c.c_int64)]),
+        "rqa_selftest_ring_timeout": (c.c_int, [vp, P(c.c_double), c.c_int64, c.c_int32,
+                                                c.c_int32]),
         "rqa_probe_alu": (c.c_int, [c.c_int32, P(c.c_double)]),
         "rqa_preload_kernels": (c.c_int, [P(c.c_int32)]),
         "rqa_autotune_last_error": (c.c_char_p, []),
@@ -236,6 +238,15 @@ class RQA:
     def _check(self, rc, where):
         if rc:
             raise RQAError(rc, where, load().rqa_last_error(self._h).decode())
+
+    def selftest_ring_timeout(self, series, warp: int = 1, from_handover: int = 3) -> int:
+        """rqa_selftest_ring_timeout: run `series` through the tile kernel's
+        test instantiation with warp `warp` withholding its hand-overs from
+        the given one on; returns the status (RQA_ETIMEOUT = 6 expected)."""
+        s = _f64(series)
+        return int(load().rqa_selftest_ring_timeout(
+            self._h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(s), warp,
+            from_handover))
 
     def set_settings(self, settings: Settings) -> None:
         """New analysis parameters for this computation (rqa_set_settings):
