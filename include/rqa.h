@@ -96,7 +96,16 @@ typedef struct {
 } rqa_settings;
 
 #define RQA_MAX_M 10
-#define RQA_MAX_N ((int64_t)1 << 22)
+/* Largest series (embedded vectors).  A single series whose strip-boundary
+ * descriptors would exceed a fifth of the device's memory (RQA_DESC_BUDGET
+ * bytes if that variable is set) runs its CTA strips in groups, carrying the
+ * open run of every row and diagonal from group to group (Sect. 4.1), so
+ * that its descriptor memory is bounded by the budget rather than growing
+ * as n^2; rqa_stats_t reports the groups and bytes. */
+#define RQA_MAX_N ((int64_t)1 << 24)
+/* Cross recurrence and precomputed matrices: rows and columns each (their
+ * strips are not grouped). */
+#define RQA_MAX_N_RECT ((int64_t)1 << 22)
 
 /* Measures (the paper's RQAResult, Sect. 7.4, Table 3).  With P_D, P_V, P_W
  * the histograms of diagonal, vertical and white vertical line lengths over
@@ -140,6 +149,12 @@ typedef struct {
   int64_t n_cols;         /* columns: n_vec for RQA, n2 for cross recurrence  */
   int64_t band_rows;      /* RQA: rows per band when strips were split into
                              row bands to fill the GPU (0: not split)         */
+  int64_t desc_bytes;     /* device bytes of strip-boundary descriptors (and
+                             group carries) the run held at once              */
+  int64_t desc_bytes_all_strips; /* the same for all strips at once          */
+  int32_t strip_groups;   /* 1, or the strip groups a long single series ran
+                             in to keep desc_bytes within the budget          */
+  int32_t strips_per_group;
 } rqa_stats_t;
 
 typedef struct rqa_handle rqa_handle;
@@ -192,7 +207,7 @@ int rqa_run_cross_device(rqa_handle* h, const double* dev_x, int64_t n_x,
  * run along all rows + cols - 1 diagonals and vertical / white lines down the
  * cols columns, as for cross recurrence, with RR = RP / (rows * cols) and
  * histograms of max(rows, cols) + 1 entries.  The handle's m, tau, eps, norm
- * and precision are not used.  rows, cols in 1..RQA_MAX_N; the library copies
+ * and precision are not used.  rows, cols in 1..RQA_MAX_N_RECT; the library copies
  * the host bits (rows * ceil(cols/32) * 4 bytes) to the device. */
 int rqa_run_matrix(rqa_handle* h, const uint32_t* host_bits, int64_t rows,
                    int64_t cols);

@@ -206,7 +206,11 @@ __device__ __forceinline__ void emit2(BlockHist& h, const SeriesDesc& S, uint32_
 // loads need not wait on each other.
 constexpr int MERGE_AHEAD = 8;
 
-__global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd) {
+// Strips q0 .. q1 of a series that runs in strip groups (q1 < 0: all strips
+// at once).  A row or diagonal that continues past the group's left edge
+// leaves its open run in rcarry / dcarry, and the next group starts from it;
+// the descriptors of strip Q sit at strip_offset(Q) - strip_offset(q0).
+__global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd, int64_t q0, int64_t q1) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || S.cross) return;
   __shared__ uint32_t sh[3 * HB];
@@ -215,11 +219,18 @@ __global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd) {
   const int64_t n = S.n, sw = S.sw;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n - 1;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t qlast = (n - 2 - i) / sw;
+    const int64_t qrow = (n - 2 - i) / sw;   // the row's last strip
+    if (qrow < q0) continue;                 // it ended in an earlier group
+    const int64_t qlast = q1 >= 0 && q1 < qrow ? q1 : qrow;
     uint32_t ocol = 0;
     uint64_t olen = 0;
-    int64_t off = i;  // strip_offset(n, sw, Q) + i, advanced strip by strip
-    for (int64_t Q0 = 0; Q0 <= qlast; Q0 += MERGE_AHEAD) {
+    if (q0 > 0) {
+      const uint32_t c = S.rcarry[i];
+      olen = c & 0x7FFFFFFFu;
+      ocol = c >> 31;
+    }
+    int64_t off = i;  // strip_offset(n, sw, Q) - strip_offset(n, sw, q0) + i
+    for (int64_t Q0 = q0; Q0 <= qlast; Q0 += MERGE_AHEAD) {
       uint32_t zs[MERGE_AHEAD], as[MERGE_AHEAD];
 #pragma unroll
       for (int u = 0; u < MERGE_AHEAD; ++u) {
@@ -259,7 +270,10 @@ __global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd) {
         }
       }
     }
-    S.rowend[i] = (uint32_t)olen | (ocol << 31);
+    if (qlast == qrow)
+      S.rowend[i] = (uint32_t)olen | (ocol << 31);
+    else
+      S.rcarry[i] = (uint32_t)olen | (ocol << 31);
   }
   h.flush(S);
 }
@@ -272,7 +286,7 @@ __global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd) {
 // Each item left the black run touching the diagonal's entry (a), the black
 // run touching its exit (z), or an all-black flag.  With one band the items
 // are the strips, Q = 0 .. (n-1-k)/sw.
-__global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd) {
+__global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd, int64_t q0, int64_t q1) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || S.cross) return;
   __shared__ uint32_t sh[3 * HB];
@@ -283,20 +297,23 @@ __global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd) {
   const int64_t H = banded ? S.band_h : n;
   for (int64_t k = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = n - 1 - k;  // entry row of the next item (-1: the walk is done)
-    uint64_t L = 0;
+    // entry row of the next item (-1: the walk is done); diagonal k enters
+    // strip Q at row n - 1 - k - Q sw
+    int64_t i = n - 1 - k - q0 * sw;
+    if (i < 0) continue;  // the diagonal ended in an earlier group
+    uint64_t L = q0 > 0 ? S.dcarry[k] : 0;
     if (!banded) {
-      // one band: the items are the strips Q = 0, 1, ... in order (the
+      // one band: the items are the strips Q = q0, q0 + 1, ... in order (the
       // diagonal leaves strip Q through its left edge J0 into strip Q + 1)
       // and band_klo is 1, so no division is needed
-      int64_t Q = 0, off = 0;  // off = strip_offset(n, sw, Q)
-      while (i >= 0) {
+      int64_t Q = q0, off = 0;  // off = strip_offset(n, sw, Q) - strip_offset(n, sw, q0)
+      while (i >= 0 && (q1 < 0 || Q <= q1)) {
         int64_t os[MERGE_AHEAD];
         int cnt = 0;
 #pragma unroll
         for (int u = 0; u < MERGE_AHEAD; ++u) {
           os[u] = -1;
-          if (i >= 0) {
+          if (i >= 0 && (q1 < 0 || Q <= q1)) {
             os[u] = off + k - 1;
             ++cnt;
             const int64_t ie = n - (Q + 1) * sw - k;  // J0 - k, the top cell's row
@@ -325,7 +342,7 @@ __global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd) {
         }
       }
     }
-    while (i >= 0) {
+    while (banded && i >= 0) {
       // the next items' descriptor positions, from the geometry alone
       int64_t os[MERGE_AHEAD];
       int cnt = 0;
@@ -363,7 +380,10 @@ __global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd) {
         }
       }
     }
-    if (L) h.add(S, HIST_DIAG, L);
+    if (i >= 0 && q1 >= 0)
+      S.dcarry[k] = (uint32_t)L;  // continues in the next group
+    else if (L)
+      h.add(S, HIST_DIAG, L);
   }
   h.flush(S);
 }
@@ -857,16 +877,28 @@ int preload_aux_kernels() {
   return static_cast<int>(sizeof(fns) / sizeof(fns[0]));
 }
 
+int launch_group_merges(SeriesDesc* d_sd, int64_t n, int64_t q0, int64_t q1, int sms,
+                        cudaStream_t st) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4 * sms) blocks = 4 * sms;
+  if (blocks < 1) blocks = 1;
+  merge_rows_kernel<<<dim3((unsigned)blocks, 1), 256, 0, st>>>(d_sd, q0, q1);
+  merge_diags_kernel<<<dim3((unsigned)blocks, 1), 256, 0, st>>>(d_sd, q0, q1);
+  return 2;
+}
+
 int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cross, bool bands,
-                  int sms, cudaStream_t st) {
+                  int sms, cudaStream_t st, bool grouped) {
   int64_t blocks = (max_n + 255) / 256;
   if (blocks > 4 * sms) blocks = 4 * sms;
   if (blocks < 1) blocks = 1;
   int launched = 0;
-  if (sym) {
-    merge_rows_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
-    merge_diags_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+  if (sym && !grouped) {
+    merge_rows_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd, 0, -1);
+    merge_diags_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd, 0, -1);
     launched += 2;
+  }
+  if (sym) {
     if (bands) {
       merge_cols_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
       ++launched;

@@ -85,6 +85,11 @@ struct Sizes {
   int64_t n = 0, n2 = 0, hl = 0, nstrips = 0, ndesc = 0, nrowdesc = 0, wpr = 0;
   int64_t nitems = 0;          // work items: strips, or (strip, band) pairs
   int64_t band_h = 0, nbands = 1;
+  // strip groups (a single RQA series whose descriptors would exceed the
+  // budget): gstrips strips per group, descriptors sized for one group
+  int64_t gstrips = 0, ngroups = 1;
+  size_t carry = 0;   // rcarry + dcarry
+  size_t desc_full = 0;  // descriptor bytes of all strips at once
   int mp = 0;
   TileConfig tc{1, 4};
   bool f64 = false, cross = false, matrix = false;
@@ -138,7 +143,7 @@ void for_each_band_item(const Sizes& z, F&& f) {
 // precomputed N x N2 bit matrix (its copy counted in `series`).
 Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross = false,
                 int64_t N2 = 0, bool copy_series2 = false, bool matrix = false,
-                int warps = 0, bool allow_bands = false, int cols = 0) {
+                int warps = 0, bool allow_bands = false, int cols = 0, size_t desc_budget = 0) {
   Sizes z;
   z.matrix = matrix;
   z.n = matrix ? N : nvec_of(st, N);
@@ -184,6 +189,27 @@ Sizes sizes_for(const rqa_settings& st, int64_t N, bool copy_series, bool cross 
   // RQA: row_a, row_z, dia_a, dia_z; cross recurrence and matrices: dia_a, dia_z
   z.desc = 2 * align256(sizeof(uint16_t) * static_cast<size_t>(z.ndesc)) +
            2 * align256(sizeof(uint16_t) * static_cast<size_t>(z.nrowdesc));
+  z.desc_full = z.desc;
+  if (desc_budget > 0 && !z.cross && z.nbands <= 1 && z.desc > desc_budget && z.nstrips > 1) {
+    // Divide & Recombine with bounded memory (Sect. 4.1's carryover buffers):
+    // the most strips per group whose descriptors fit the budget (the first
+    // group, of the tallest strips, is the largest)
+    const int64_t sw = 32LL * z.tc.warps * z.tc.cols;
+    int64_t lo = 1, hi = z.nstrips;  // the largest g with 8 bytes per descriptor in budget
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo + 1) / 2;
+      if (static_cast<size_t>(strip_offset(z.n, sw, mid)) * 8 <= desc_budget)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const int64_t g = lo;
+    z.gstrips = g;
+    z.ngroups = (z.nstrips + g - 1) / g;
+    z.ndesc = z.nrowdesc = strip_offset(z.n, sw, g);
+    z.desc = 4 * align256(sizeof(uint16_t) * static_cast<size_t>(z.ndesc));
+    z.carry = 2 * align256(sizeof(uint32_t) * static_cast<size_t>(z.n));
+  }
   if (matrix) {
     z.wpr = (z.n2 + 31) / 32;
     z.series = copy_series ? align256(sizeof(uint32_t) * static_cast<size_t>(z.n * z.wpr)) : 0;
@@ -209,8 +235,8 @@ int validate_input(const SeriesInput& in, std::string* msg) {
       *msg = "matrix has no rows or no columns";
       return RQA_ESHORT;
     }
-    if (in.N > RQA_MAX_N || in.N2 > RQA_MAX_N) {
-      *msg = "more than RQA_MAX_N rows or columns";
+    if (in.N > RQA_MAX_N_RECT || in.N2 > RQA_MAX_N_RECT) {
+      *msg = "more than RQA_MAX_N_RECT rows or columns";
       return RQA_ETOOBIG;
     }
     return RQA_OK;
@@ -231,6 +257,10 @@ int validate_input(const SeriesInput& in, std::string* msg) {
     *msg = "more than RQA_MAX_N embedded vectors";
     return RQA_ETOOBIG;
   }
+  if (in.cross && nvec_of(in.st, in.N) > RQA_MAX_N_RECT) {
+    *msg = "more than RQA_MAX_N_RECT embedded vectors in the first series";
+    return RQA_ETOOBIG;
+  }
   if (in.cross) {
     if (!in.host2 && !in.dev2) {
       *msg = "second series pointer is NULL";
@@ -240,8 +270,8 @@ int validate_input(const SeriesInput& in, std::string* msg) {
       *msg = "second series shorter than the embedding window (m-1)*tau + 1";
       return RQA_ESHORT;
     }
-    if (nvec_of(in.st, in.N2) > RQA_MAX_N) {
-      *msg = "more than RQA_MAX_N embedded vectors in the second series";
+    if (nvec_of(in.st, in.N2) > RQA_MAX_N_RECT) {
+      *msg = "more than RQA_MAX_N_RECT embedded vectors in the second series";
       return RQA_ETOOBIG;
     }
   }
@@ -415,6 +445,23 @@ void Engine::free_arena(cudaStream_t st) {
 // Grow the arena to at least `bytes` (by half again, so growth stays rare).
 // From the pool, the old block is released and the new one taken in the
 // order of `st`, which every previous run of this engine has completed on.
+// Boundary-descriptor budget of a single RQA series, above which its strips
+// run in groups: RQA_DESC_BUDGET bytes if set, else a fifth of the device's
+// memory (55 GB on a B300: the 1,048,576-point series, 4.3 GB, runs in one
+// group; 2^22 vectors, 69 GB, in three).
+size_t Engine::desc_budget() const {
+  if (const char* e = std::getenv("RQA_DESC_BUDGET")) {
+    const long long b = std::atoll(e);
+    if (b > 0) return static_cast<size_t>(b);
+  }
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return size_t(16) << 30;
+  }
+  return tot / 5;
+}
+
 int Engine::ensure_arena(size_t bytes, cudaStream_t st) {
   if (bytes <= arena_cap_) return RQA_OK;
   if (graph_) {
@@ -423,7 +470,9 @@ int Engine::ensure_arena(size_t bytes, cudaStream_t st) {
     graph_key_.clear();
   }
   free_arena(st);
-  const size_t cap = bytes + bytes / 2;
+  // room to grow by half again, at most 1 GiB more (large series run in
+  // strip groups whose arena is sized by the descriptor budget)
+  const size_t cap = bytes + std::min<size_t>(bytes / 2, size_t(1) << 30);
   void* p = nullptr;
   cudaError_t e = pool_ ? cudaMallocFromPoolAsync(&p, cap, pool_, st) : cudaMalloc(&p, cap);
   if (e != cudaSuccess) {
@@ -492,7 +541,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     Sizes z;
     int cls = -1;
     bool run = false;
-    size_t o_hist, o_ends, o_cnt, o_desc, o_series, o_series2, o_xe, o_xe2, o_tab, o_cols;
+    size_t o_hist, o_ends, o_cnt, o_desc, o_series, o_series2, o_xe, o_xe2, o_tab, o_cols,
+        o_carry;
   };
   std::vector<P> plan(count);
   std::vector<int> dev_idx(count, -1);  // device slot of each runnable series
@@ -572,7 +622,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
                       warps, bands_ok, cols);
     else
       p.z = sizes_for(in[q].st, in[q].N, in[q].dev == nullptr, in[q].cross, in[q].N2,
-                      in[q].dev2 == nullptr, false, warps, bands_ok, cols);
+                      in[q].dev2 == nullptr, false, warps, bands_ok, cols,
+                      count == 1 && in[q].withhold_warp == 0 ? desc_budget() : 0);
     dev_idx[q] = nrun++;
     // kernel class: (m, norm, f64, warps, kind, columns per lane), kind 0
     // RQA, 1 cross, 2 matrix, plus 3 for the row-band instantiation of each
@@ -657,9 +708,12 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       p.o_tab = off;
       off += p.z.tab;
     }
+  // a single RQA series may run in strip groups, one tile launch (and work
+  // queue counter) per group
+  const int64_t ngroups = (count == 1 && plan[0].run) ? plan[0].z.ngroups : 1;
   const size_t o_zero = off;
   const size_t o_queue = off;
-  off += align256(sizeof(int) * ncls);
+  off += align256(sizeof(int) * static_cast<size_t>(ncls + ngroups));
   const size_t o_hist0 = off;  // per group: [histograms][counters]
   size_t hist_bytes = 0, cnt_bytes = 0;
   for (Grp& gr : grp) {
@@ -684,6 +738,8 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       off += p.z.ends;
       p.o_desc = off;
       off += p.z.desc;
+      p.o_carry = off;
+      off += p.z.carry;
       p.o_cols = off;
       off += p.z.cols;
     }
@@ -801,6 +857,10 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
         d.row_z = reinterpret_cast<uint16_t*>(arena_ + p.o_desc + 2 * dbytes + rbytes);
         d.colend = reinterpret_cast<uint32_t*>(arena_ + p.o_ends);
         d.rowend = d.colend + p.z.n;
+        if (p.z.carry) {
+          d.rcarry = reinterpret_cast<uint32_t*>(arena_ + p.o_carry);
+          d.dcarry = reinterpret_cast<uint32_t*>(arena_ + p.o_carry + p.z.carry / 2);
+        }
       }
     }
     d.counters = reinterpret_cast<unsigned long long*>(arena_ + p.o_cnt);
@@ -828,9 +888,12 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
                                            static_cast<int32_t>(g)}});
         });
       } else {
-        for (int64_t Q = 0; Q < p.z.nstrips; ++Q)  // strip height: the rows it spans
+        for (int64_t Q = 0; Q < p.z.nstrips; ++Q) {  // strip height: the rows it spans
+          const int64_t base = p.z.gstrips > 0 ? Q / p.z.gstrips * p.z.gstrips : 0;
           per[p.cls].push_back({p.z.cross ? p.z.n : p.z.n - Q * sw,
-                                Item{dev_idx[q], static_cast<int32_t>(Q), 0}});
+                                Item{dev_idx[q], static_cast<int32_t>(Q), 0,
+                                     static_cast<int32_t>(base)}});
+        }
       }
     }
     int64_t pos = 0;
@@ -937,6 +1000,34 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
                &per_sm, reinterpret_cast<const void*>(fn), 32 * warps, smem)) != cudaSuccess)
         return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
       const int64_t nit = cls_start[c + 1] - cls_start[c];
+      if (ngroups > 1) {
+        // one series in strip groups (Sect. 4.1, Divide & Recombine with
+        // carryover buffers): per group, the tile kernel over its strips
+        // (their descriptors from the start of the buffer), then the row and
+        // diagonal merges, which carry open runs to the next group
+        const P& p = plan[0];
+        for (int64_t gi = 0; gi < ngroups; ++gi) {
+          const int64_t q0 = gi * p.z.gstrips;
+          const int64_t q1 = std::min(p.z.nstrips, q0 + p.z.gstrips) - 1;
+          if (gi > 0 &&
+              (e = cudaMemsetAsync(arena_ + p.o_desc, 0, p.z.desc, st)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemsetAsync(group descriptors)");
+          const int64_t gn = q1 - q0 + 1;
+          const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(gn, (int64_t)per_sm * sms_));
+          const SeriesDesc* a_sd = d_sd;
+          const Item* a_items = d_items + cls_start[c] + q0;
+          int a_n = static_cast<int>(gn);
+          int* a_queue = d_queue + ncls + gi;
+          void* args[] = {&a_sd, &a_items, &a_n, &a_queue};
+          if ((e = cudaLaunchKernel(reinterpret_cast<const void*>(fn),
+                                    dim3(static_cast<unsigned>(grid)), dim3(32 * warps), args,
+                                    smem, st)) != cudaSuccess)
+            return cuda_fail(e, "tile kernel launch");
+          launches += 1 + launch_group_merges(d_sd, p.z.n, q0, q1, sms_, st);
+          ctas_total += grid;
+        }
+        continue;
+      }
       const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nit, (int64_t)per_sm * sms_));
       const SeriesDesc* a_sd = d_sd;
       const Item* a_items = d_items + cls_start[c];
@@ -959,7 +1050,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
         return cuda_fail(e, "cudaEventRecord");
       if (gr.count > 0) {
         launches += launch_merges(d_sd + gr.first, gr.count, gr.max_n, gr.sym, gr.cross,
-                                  gr.bands, sms_, gs);
+                                  gr.bands, sms_, gs, ngroups > 1);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "merge kernels launch");
         if ((e = cudaMemcpyAsync(host_ + h_hist + (gr.o_rb - o_hist0), arena_ + gr.o_rb,
                                  gr.rb_bytes, cudaMemcpyDeviceToHost, gs)) != cudaSuccess)
@@ -1063,6 +1154,10 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
     s.exact = (p.z.f64 || p.z.matrix || d.band_rel >= d.bound_rel) ? 1 : 0;
     s.strip_width = 32 * p.z.tc.warps * p.z.tc.cols;
     s.band_rows = p.z.nbands > 1 ? p.z.band_h : 0;
+    s.desc_bytes = static_cast<int64_t>(p.z.desc + p.z.carry);
+    s.desc_bytes_all_strips = static_cast<int64_t>(p.z.desc_full);
+    s.strip_groups = static_cast<int32_t>(p.z.ngroups);
+    s.strips_per_group = static_cast<int32_t>(p.z.gstrips > 0 ? p.z.gstrips : p.z.nstrips);
     s.warps_per_cta = p.z.tc.warps;
     s.cols_per_lane = p.z.tc.cols;
     s.h2d_bytes = static_cast<int64_t>((o_zero - o_sd) + series_bytes);

@@ -116,6 +116,7 @@ class Engine {
   int run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& results,
                cudaStream_t stream, bool use_graph);
   int ensure_arena(size_t bytes, cudaStream_t st);
+  size_t desc_budget() const;
   int ensure_host(size_t bytes);
   void free_arena(cudaStream_t st);
   int fail(int code, const std::string& msg);

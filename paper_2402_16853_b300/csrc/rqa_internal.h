@@ -50,6 +50,12 @@ struct SeriesDesc {
   uint16_t* dia_z;
   uint32_t* colend;           // [n] run of column j touching row j-1
   uint32_t* rowend;           // [n] run of row i touching column i+1
+  // strip groups (Divide & Recombine, Sect. 4.1): a series whose boundary
+  // descriptors would exceed the memory budget runs G strips at a time; the
+  // run of each row and each diagonal left open at a group's left edge is
+  // carried to the next group here (length | colour << 31; diagonals: length)
+  uint32_t* rcarry;           // [n]
+  uint32_t* dcarry;           // [n]
   unsigned long long* counters;  // [0] rechecks, [1] status (rqa_status)
   // ---- test of the bounded ring waits (read only by the test instantiation
   // of the tile kernel; 0 = off): warp withhold_warp - 1 of every CTA stops
@@ -108,6 +114,8 @@ struct Item {
   int32_t series;
   int32_t strip;
   int32_t band;
+  int32_t base;   // first strip of the item's strip group (0 unless the series
+                  // runs in groups; its descriptors start at that strip's)
 };
 
 // Diagonals k >= 1 that can cross item (Q, g) of an RQA strip [J1 - sw, J1)

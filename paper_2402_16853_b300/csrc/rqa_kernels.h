@@ -37,7 +37,12 @@ void launch_embed(SeriesDesc* d_sd, int count, int64_t max_n_mp, int sms, cudaSt
 // row bands (column joins); max_n bounds the rows, columns and diagonals of
 // any series.  Returns the number of kernels launched.
 int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cross, bool bands,
-                  int sms, cudaStream_t st);
+                  int sms, cudaStream_t st, bool grouped = false);
+// A single RQA series run in strip groups: the row and diagonal merges of
+// strips q0 .. q1 (carries in rcarry / dcarry); launch_merges(..., grouped)
+// then does the rest after the last group.  Returns the kernels launched.
+int launch_group_merges(SeriesDesc* d_sd, int64_t n, int64_t q0, int64_t q1, int sms,
+                        cudaStream_t st);
 void launch_plot(const SeriesDesc* d_sd, int64_t i0, int64_t j0, int64_t rows, int64_t cols,
                  uint32_t* out, int f64, int m, int norm, int sms, cudaStream_t st);
 // Bounded-wait self-test (status[3] in device memory: status, cycles, abort).

@@ -580,7 +580,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
     // banded: per item, from the series' item table)
     const int64_t off = banded ? Sp->dia_off[(int64_t)wi.strip * Sp->nbands + g]
                         : XR   ? (int64_t)wi.strip * cross_strip_diags(n, SW)
-                               : strip_offset(n, SW, wi.strip);
+                               : strip_offset(n, SW, wi.strip) - strip_offset(n, SW, wi.base);
     const int klo = XR ? J1 - SW - (R1 - 1) : banded ? (int)band_klo(J1, SW, R1) : 1;
     // row descriptors keep the strip-triangular layout (rows never cross bands)
     const int64_t roff = (banded && !XR) ? strip_offset(n, SW, wi.strip) : off;

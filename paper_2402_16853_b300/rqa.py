@@ -85,7 +85,9 @@ class _CStats(ctypes.Structure):
                 ("total_ms", ctypes.c_float), ("h2d_bytes", ctypes.c_int64),
                 ("d2h_bytes", ctypes.c_int64), ("launches", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("n_cols", ctypes.c_int64),
-                ("band_rows", ctypes.c_int64)]
+                ("band_rows", ctypes.c_int64), ("desc_bytes", ctypes.c_int64),
+                ("desc_bytes_all_strips", ctypes.c_int64), ("strip_groups", ctypes.c_int32),
+                ("strips_per_group", ctypes.c_int32)]
 
 
 MEASURE_FIELDS = list(_MEAS_D + _MEAS_I)

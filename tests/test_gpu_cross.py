@@ -206,7 +206,7 @@ def test_medium_lorenz_streaming_oracle():
 
 
 def test_max_rows_rectangle():
-    """n1 = RQA_MAX_N = 2^22 row vectors against n2 = 2^20 column vectors
+    """n1 = RQA_MAX_N_RECT = 2^22 row vectors against n2 = 2^20 column vectors
     (4.4e12 cells): every cell lies in exactly one vertical black or white
     run of its column, the diagonal and vertical scans see the same
     recurrence points, and sampled decisions (uniform and near the radius)

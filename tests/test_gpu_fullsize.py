@@ -153,21 +153,23 @@ def test_paper_sine_series():
     assert np.all(off % 2 == 0)                   # the two triangles mirror each other
 
 
-def test_max_size_series():
-    """n = RQA_MAX_N = 2^22 vectors (include/rqa.h), the largest series the
-    library accepts: about 8.8e12 pairs and 69 GB of strip-boundary
-    descriptors.  The same size-independent properties as above hold, and
-    sampled decisions (uniform, near the line of identity, near the radius)
-    equal the oracle's; one vector more is rejected."""
-    max_n = 1 << 22
+def _large_series_checks(n_vec, seed, expect_groups):
+    """A series of n_vec AR(1) vectors: it runs in strip groups (its
+    boundary descriptors would exceed the budget), holds at most the budget
+    at once, and the size-independent properties hold; sampled decisions
+    (uniform, near the line of identity, near the radius) equal the
+    oracle's."""
     m, tau = 3, 1
-    s = synth.ar1(max_n + (m - 1) * tau, 1009, 0.95)
+    s = synth.ar1(n_vec + (m - 1) * tau, seed, 0.95)
     p = dict(m=m, tau=tau, eps=0.5, norm=1, theiler=1)
     r = gp.RQA(gp.Settings(**p))
     meas = r.run(s)
     hd, hv, hw = r.histograms()
     st = r.stats()
-    n = max_n
+    n = n_vec
+    assert st["strip_groups"] >= expect_groups
+    assert st["desc_bytes"] < st["desc_bytes_all_strips"]
+    assert st["strip_groups"] * st["strips_per_group"] * st["strip_width"] >= n - 1
     assert st["n_vec"] == n and meas["n_vec"] == n
     L = np.arange(n + 1, dtype=np.uint64)
     rp = int((L * hv).sum())
@@ -191,6 +193,44 @@ def test_max_size_series():
                      and abs(a - b) >= p["theiler"] for a, b in zip(i, j)], dtype=np.uint8)
     assert np.array_equal(got, want)
     r.close()
+
+
+def test_series_of_2_22_vectors():
+    """n = 2^22 vectors: about 8.8e12 pairs; all its strips' boundary
+    descriptors would take 69 GB, so it runs in strip groups under the
+    default budget (a fifth of the device's memory)."""
+    _large_series_checks(1 << 22, 1009, 2)
+
+
+def test_series_of_2_23_vectors():
+    """n = 2^23 vectors (3.5e13 pairs, 275 GB of descriptors for all
+    strips at once, above the device's memory): strip groups bound it."""
+    _large_series_checks(1 << 23, 1015, 5)
+
+
+def test_largest_accepted_size():
+    """RQA_MAX_N = 2^24 vectors is the largest series accepted; one vector
+    more is refused before anything runs."""
+    p = dict(m=3, tau=1, eps=0.5, norm=1, theiler=1)
+    s = np.zeros((1 << 24) + 3)
     with pytest.raises(gp.RQAError) as e:
-        gp.RQA(gp.Settings(**p)).run(np.concatenate([s, [0.0]]))
+        gp.RQA(gp.Settings(**p)).run(s)
     assert e.value.status == 9  # RQA_ETOOBIG
+
+
+def test_ar1_n1m_in_strip_groups_equals_full_oracle(monkeypatch):
+    """The 1,048,576-point workload with the descriptor budget forced down to
+    1.1 GB: its 1,024 strips run in groups, rows and diagonals carried from
+    group to group, and the histograms still equal the oracle's complete
+    result bit for bit."""
+    monkeypatch.setenv("RQA_DESC_BUDGET", str(1_100_000_000))
+    s, p = synth.workload("ar1_n1m")
+    r = gp.RQA(gp.Settings(**p))
+    meas = r.run(s)
+    st = r.stats()
+    assert st["strip_groups"] >= 4 and st["desc_bytes"] <= 1_100_000_000 + 2 * 4 * st["n_vec"] + 4096
+    gold = json.load(open(GOLDEN))
+    for name, h in zip(("hd", "hv", "hw"), r.histograms()):
+        assert hashlib.sha256(np.ascontiguousarray(h, dtype="<u8").tobytes()).hexdigest() \
+            == gold[name]["sha256"], name
+    assert_same_measures(meas, gold["measures"])
