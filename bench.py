@@ -565,6 +565,15 @@ def bench_batch(gp, args, dev, barrier):
         res2, st2, rc2 = b.run(settings, series)
     t_batch = (time.perf_counter() - t0) / steps
     bst = b.stats()
+    untuned = None
+    if tuned:  # the same batch with the size rule only (tuning table cleared)
+        gp.autotune_clear()
+        b.run(settings, series)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            b.run(settings, series)
+        untuned = len(series) / ((time.perf_counter() - t0) / steps)
+        gp.load_tuning_table(gp.rqa.TUNING_TABLE)
     # sequential single-series calls of the same kernels on one prebuilt
     # handle (rqa_set_settings between series), its buffers already grown to
     # the largest series, so only the per-series launch work is timed
@@ -589,7 +598,8 @@ def bench_batch(gp, args, dev, barrier):
             "speedup_vs_sequential": t_seq / t_batch, "identical_to_sequential": bool(same),
             "sequential_baseline": "rqa_run per series on one prebuilt handle "
                                    "(rqa_set_settings between series)",
-            "tuned": tuned,
+            "tuned": tuned, "untuned_series_per_s": untuned,
+            "speedup_tuned_vs_untuned": (len(series) / t_batch) / untuned if untuned else None,
             "graph": "captured once, replayed",
             "cpu_oracle": batch_oracle_sample(specs, series, eps) if not args.no_cpu else None}
 
