@@ -238,11 +238,14 @@ __device__ __forceinline__ uint32_t scan2(uint32_t x, int hi, int lo, uint32_t s
 
 // Lines of length 1..3 are counted without emitting them one by one: 16-bit
 // fields packed two per register, added to the histograms every
-// FLUSH_BLOCKS blocks (at most 128 per field per block, so no field wraps).
+// FLUSH_BLOCKS blocks.  The two-colour fields count black runs and runs of
+// both colours (white = both - black at the flush): a 32-cell word holds at
+// most 30 interior runs of one length, a block at most 8 two-colour words,
+// so a field gains at most 240 per block and 61,440 < 2^16 between flushes.
 struct ShortCounts {
   uint32_t v12;   // vertical black: length 1 | length 2 << 16
-  uint32_t v3w1;  // vertical black length 3 | white length 1 << 16
-  uint32_t w23;   // white: length 2 | length 3 << 16
+  uint32_t v3w1;  // vertical black length 3 | both colours length 1 << 16
+  uint32_t w23;   // both colours: length 2 | length 3 << 16
   uint32_t d12;   // diagonal: length 1 | length 2 << 16
   uint32_t d3;    // diagonal: length 3
 };
@@ -273,17 +276,18 @@ __device__ __forceinline__ uint32_t scan2_full(uint32_t x, uint32_t st, ShortCou
   const int ptop = msb(T);
   const uint32_t toplen = cl + (uint32_t)(32 - ptop);
   if (fl) first(ctop, toplen); else emit(ctop, toplen);
-  const uint32_t S = T ^ (1u << ptop);  // lowest cells of the interior runs
   {  // unconditional: with no interior run every count below is zero
+    // interior runs start (lowest cell) at every transition but the top
+    // one, which the masks below never select (no transition lies above it)
     const uint32_t t1 = T >> 1, t2 = T >> 2, t3 = T >> 3;
-    const uint32_t l1 = S & t1;
-    const uint32_t l2 = S & t2 & ~t1;
-    const uint32_t l3 = S & t3 & ~(t1 | t2);
+    const uint32_t l1 = T & t1;
+    const uint32_t l2 = T & t2 & ~t1;
+    const uint32_t l3 = T & t3 & ~(t1 | t2);
     sc.v12 += __popc(l1 & x) + (__popc(l2 & x) << 16);
-    sc.v3w1 += __popc(l3 & x) + (__popc(l1 & ~x) << 16);
-    sc.w23 += __popc(l2 & ~x) + (__popc(l3 & ~x) << 16);
-    uint32_t lg = S & ~(t1 | t2 | t3);
-    while (lg) {
+    sc.v3w1 += __popc(l3 & x) + (__popc(l1) << 16);
+    sc.w23 += __popc(l2) + (__popc(l3) << 16);
+    uint32_t lg = T & ~(t1 | t2 | t3);  // and the top transition, never taken
+    while (lg & (lg - 1u)) {
       // lowest cell q of a run of length >= 4 whose upper end is a transition
       // below bit 32: in the word of the run's colour as ones, adding 2^q
       // carries through the run and stops at that transition, so the bits
@@ -345,9 +349,9 @@ __device__ __forceinline__ void flush_short(ShortCounts& sc, uint32_t* sh_hist, 
   flush_one(sc.v12 & 0xFFFFu, sh_hist + HIST_VERT * HB + 1, lane);
   flush_one(sc.v12 >> 16, sh_hist + HIST_VERT * HB + 2, lane);
   flush_one(sc.v3w1 & 0xFFFFu, sh_hist + HIST_VERT * HB + 3, lane);
-  flush_one(sc.v3w1 >> 16, sh_hist + HIST_WHITE * HB + 1, lane);
-  flush_one(sc.w23 & 0xFFFFu, sh_hist + HIST_WHITE * HB + 2, lane);
-  flush_one(sc.w23 >> 16, sh_hist + HIST_WHITE * HB + 3, lane);
+  flush_one((sc.v3w1 >> 16) - (sc.v12 & 0xFFFFu), sh_hist + HIST_WHITE * HB + 1, lane);
+  flush_one((sc.w23 & 0xFFFFu) - (sc.v12 >> 16), sh_hist + HIST_WHITE * HB + 2, lane);
+  flush_one((sc.w23 >> 16) - (sc.v3w1 & 0xFFFFu), sh_hist + HIST_WHITE * HB + 3, lane);
   flush_one(sc.d12 & 0xFFFFu, sh_hist + HIST_DIAG * HB + 1, lane);
   flush_one(sc.d12 >> 16, sh_hist + HIST_DIAG * HB + 2, lane);
   flush_one(sc.d3, sh_hist + HIST_DIAG * HB + 3, lane);
@@ -505,6 +509,7 @@ __global__ void __launch_bounds__(256, 3)
 tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, int nitems,
             int* __restrict__ queue) {
   constexpr long long spin_limit = TW ? TEST_SPIN_CYCLES : SPIN_CYCLES;
+  static_assert(C <= 4, "the short-run counters are flushed for at most 8 two-colour words a block");
   using T = typename std::conditional<F64, double, float>::type;
   constexpr int RE = tile_row_elems<M, NORM, F64>();
   constexpr bool PACKED = !F64 && NORM != 2 && (C % 2 == 0);  // L2 and L-infinity
@@ -901,6 +906,37 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
               transpose32x2(RW, D, lane);
             else
               D = transpose32(D, lane);
+          }
+          if constexpr (!XR && !MX) {
+            // two or more blocks right of the diagonal (almost every
+            // sub-block): every column and row word is full, no row ends
+            // here, so the per-lane geometry below is not needed (5 % of the
+            // 1M-point kernel's time)
+            if (col0 - r0 >= 64) {
+              auto emit2 = [&](uint32_t col, uint32_t len) { hs.add2(col, len); };
+              cst_s[c * 32 + lane] = scan2_full(
+                  R, cst_s[c * 32 + lane], sc, hs, emit2,
+                  [&](uint32_t col, uint32_t len) { colfirst[j] = len | (col << 31); });
+              rst = scan2_full(RW, rst, sc, hs, emit2, [&](uint32_t col, uint32_t len) {
+                row_a[roff + irow] = (uint16_t)((len << 1) | col);
+              });
+              const int k = col0 - r0 + d;
+              auto emitd = [&](uint32_t len) { hs.add(HIST_DIAG, len); };
+              auto firstd = [&](uint32_t len) {
+                if (k >= klo) dia_a[off + k - klo] = (uint16_t)len;
+              };
+              if (c == C - 1) {
+                dU_new[c * 32 + lane] =
+                    scanb_full(D | segL, dL, sc, hs, emitd, firstd) - (uint32_t)d;
+              } else {
+                const uint32_t w = (Dprev & segL) | (D & segU);
+                dU_new[c * 32 + lane] = scanb_full(__funnelshift_r(w, w, d),
+                                                   dU_old[(c + 1) * 32 + lane], sc, hs, emitd, firstd);
+              }
+              Dprev = D;
+              hs.drain(lane);
+              continue;
+            }
           }
 
           // ---- operator III, upper part of full column j (rows < j); cross:
