@@ -121,7 +121,7 @@ int rqa_set_settings(rqa_handle* h, const rqa_settings* settings) {
 
 static int run_input(rqa_handle* h, std::vector<rqa::SeriesInput>& in, void* stream) {
   std::vector<rqa::SeriesResult> res;
-  int rc = h->eng->run(in, res, static_cast<cudaStream_t>(stream), false);
+  int rc = h->eng->run(in, res, static_cast<cudaStream_t>(stream), rqa::Engine::kGraphOnRepeat);
   if (rc != RQA_OK) {
     h->err = h->eng->error();
     return rc;
@@ -302,7 +302,7 @@ int rqa_selftest_ring_timeout(rqa_handle* h, const double* host_series, int64_t 
   in[0].withhold_seq = from_handover;
   rqa::tune_force(8, 4, 0);  // eight warps per strip, so the warp has a consumer
   std::vector<rqa::SeriesResult> res;
-  const int rc = h->eng->run(in, res, nullptr, false);
+  const int rc = h->eng->run(in, res, nullptr, rqa::Engine::kNoGraph);
   rqa::tune_force_clear();
   if (rc != RQA_OK) {
     h->err = h->eng->error();
@@ -349,7 +349,7 @@ int batch_run_on(rqa_batch* b, const rqa_settings* settings, const double* const
     in[q].host = series[q];
     in[q].N = lens[q];
   }
-  int rc = b->eng->run(in, b->res, stream, true);
+  int rc = b->eng->run(in, b->res, stream, rqa::Engine::kGraph);
   b->err = b->eng->error();
   b->stats = rqa_stats_t{};
   for (int32_t q = 0; q < count && q < static_cast<int32_t>(b->res.size()); ++q) {

@@ -508,8 +508,8 @@ int Engine::ensure_host(size_t bytes) {
 }
 
 int Engine::run(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& results,
-                cudaStream_t stream, bool use_graph) {
-  const int rc = run_impl(in, results, stream, use_graph);
+                cudaStream_t stream, GraphMode mode) {
+  const int rc = run_impl(in, results, stream, mode);
   if (rc != RQA_OK) {
     // a failure of the whole set marks every unfinished series
     for (auto& r : results)
@@ -523,7 +523,7 @@ int Engine::run(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& r
 }
 
 int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& results,
-                     cudaStream_t stream, bool use_graph) {
+                     cudaStream_t stream, GraphMode mode) {
   err_.clear();
   cudaError_t ce = cudaSetDevice(dev_);
   if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
@@ -913,7 +913,7 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   int* d_queue = reinterpret_cast<int*>(arena_ + o_queue);
 
   std::vector<int64_t> key;
-  if (use_graph) {
+  if (mode != kNoGraph) {
     key.push_back(count);
     key.push_back(reinterpret_cast<int64_t>(arena_));
     key.push_back(reinterpret_cast<int64_t>(host_));
@@ -934,11 +934,16 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       key.push_back(plan[q].run ? plan[q].z.tc.warps : 0);
       key.push_back(plan[q].run ? plan[q].z.tc.cols : 0);
       key.push_back(plan[q].run ? plan[q].z.band_h : 0);
+      key.push_back(plan[q].run ? plan[q].z.gstrips : 0);  // strip groups (descriptor budget)
       key.push_back(in[q].N2);
       key.push_back(reinterpret_cast<int64_t>(in[q].dev2));
     }
   }
-  const bool replay = use_graph && graph_ && key == graph_key_;
+  const bool cached = graph_ && key == graph_key_;
+  const bool use_graph =
+      mode == kGraph || (mode == kGraphOnRepeat && (cached || (!key.empty() && key == prev_key_)));
+  if (mode == kGraphOnRepeat && !use_graph) prev_key_ = key;
+  const bool replay = use_graph && cached;
 
   // timing events are external nodes when captured, so replays record them
   const unsigned evflags = use_graph ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -1093,6 +1098,11 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
         return cuda_fail(e, "cudaGraphInstantiate");
       }
       graph_key_ = key;
+      graph_launches_ = launches;
+      graph_ctas_ = ctas_total;
+    } else {
+      launches = graph_launches_;  // the kernels the replayed graph launches
+      ctas_total = graph_ctas_;
     }
     cudaError_t e = cudaGraphLaunch(graph_, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");

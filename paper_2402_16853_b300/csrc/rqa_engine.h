@@ -96,11 +96,17 @@ class Engine {
   Engine(const Engine&) = delete;
   Engine& operator=(const Engine&) = delete;
 
+  // How a run's launch sequence is issued: as plain launches, always through
+  // a cached CUDA graph (captured when the plan changes), or through the graph
+  // from the second consecutive run with the same plan (single-series calls:
+  // a one-off run pays no capture, a repeated one no launch overhead).
+  enum GraphMode { kNoGraph = 0, kGraph = 1, kGraphOnRepeat = 2 };
+
   // Run a set of series on `stream` (nullptr: the engine's own stream).
   // Returns RQA_OK if the set ran (per-series failures are in
   // results[q].status), or an error that affected the whole set.
   int run(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& results,
-          cudaStream_t stream, bool use_graph);
+          cudaStream_t stream, GraphMode mode);
 
   // Decisions R_ij of series 0 of the last run (needs its buffers alive;
   // RQA_EINVAL after a precomputed-matrix run, which has no decisions).
@@ -114,7 +120,7 @@ class Engine {
 
  private:
   int run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& results,
-               cudaStream_t stream, bool use_graph);
+               cudaStream_t stream, GraphMode mode);
   int ensure_arena(size_t bytes, cudaStream_t st);
   size_t desc_budget() const;
   int ensure_host(size_t bytes);
@@ -148,9 +154,13 @@ class Engine {
   bool last_f64_ = false;
   bool last_matrix_ = false;
   cudaStream_t last_stream_ = nullptr;
-  // graph cache (batched runs with an unchanged plan)
+  // graph cache (runs with an unchanged plan); prev_key_: the plan of the
+  // last run issued without the graph, for kGraphOnRepeat
   cudaGraphExec_t graph_ = nullptr;
   std::vector<int64_t> graph_key_;
+  std::vector<int64_t> prev_key_;
+  int graph_launches_ = 0;      // kernel launches and CTAs of the cached graph
+  int64_t graph_ctas_ = 0;
 };
 
 }  // namespace rqa

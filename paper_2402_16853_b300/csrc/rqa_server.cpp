@@ -103,7 +103,7 @@ void rqa_server::worker(int idx) {
       in[q].N = static_cast<int64_t>(epoch[q]->series.size());
     }
     std::vector<rqa::SeriesResult> res;
-    const int rc = eng.run(in, res, nullptr, false);
+    const int rc = eng.run(in, res, nullptr, rqa::Engine::kNoGraph);
     {
       std::lock_guard<std::mutex> lk(mu);
       for (size_t q = 0; q < epoch.size(); ++q) {

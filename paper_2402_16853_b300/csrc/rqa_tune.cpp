@@ -121,7 +121,7 @@ float time_shape(rqa::Engine& eng, const std::vector<rqa::SeriesInput>& in,
   rqa::tune_force(c.warps, c.cols, c.band_scale);
   float t = INFINITY;
   for (int rep = 0; rep < 3 && *rc == RQA_OK; ++rep) {
-    *rc = eng.run(in, res, nullptr, false);
+    *rc = eng.run(in, res, nullptr, rqa::Engine::kNoGraph);
     if (*rc == RQA_OK && rep > 0) t = std::fmin(t, eng.last_total_ms());
   }
   rqa::tune_force_clear();
