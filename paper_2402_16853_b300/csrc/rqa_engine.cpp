@@ -388,6 +388,7 @@ Engine::Engine(int device) : dev_(device) {
   for (auto& e : ev_) cudaEventCreate(&e);
   for (auto& a : aux_) cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking);
   cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&order_, cudaEventDisableTiming);
   for (auto& j : join_) cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
   for (auto& t : tiled_) cudaEventCreate(&t);
   for (auto& d : done_) cudaEventCreateWithFlags(&d, cudaEventDisableTiming);
@@ -413,6 +414,7 @@ Engine::~Engine() {
   for (auto& d : done_)
     if (d) cudaEventDestroy(d);
   if (fork_) cudaEventDestroy(fork_);
+  if (order_) cudaEventDestroy(order_);
   free_arena(own_);  // every run ended with its stream idle
   cudaStreamSynchronize(own_);
   if (pool_) cudaMemPoolDestroy(pool_);
@@ -1074,6 +1076,20 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
       return cuda_fail(e, "cudaEventRecord");
     return RQA_OK;
   };
+
+  // A caller's device series, with no stream given: the entry points order
+  // the run on the legacy default stream, so the engine's own (non-blocking)
+  // stream first waits for the work queued there (the series may still be
+  // being written by it).  Outside any capture: a replay needs it as well.
+  if (!stream) {
+    bool dev_in = false;
+    for (const auto& x : in) dev_in = dev_in || x.dev || x.dev2 || x.bits_dev;
+    if (dev_in) {
+      cudaError_t e = cudaEventRecord(order_, cudaStreamLegacy);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, order_, 0);
+      if (e != cudaSuccess) return cuda_fail(e, "ordering after the legacy default stream");
+    }
+  }
 
   if (use_graph) {
     if (!replay) {

@@ -142,6 +142,7 @@ class Engine {
   static constexpr int kAux = 4;
   cudaStream_t aux_[kAux] = {};
   cudaEvent_t fork_ = nullptr;
+  cudaEvent_t order_ = nullptr;  // orders the own stream after the legacy default stream
   cudaEvent_t join_[kAux] = {};
   // per stream group: its tile kernels are done (timing) / its histograms
   // and counters have landed in the pinned staging (waited on by the host)

@@ -76,3 +76,24 @@ def test_cross_repeated():
         want = oracle.cross_rqa(x, y, oracle_settings(**kw))
         assert np.array_equal(r.histogram(0), want["hd"])
         assert_same_measures(meas, want["measures"])
+
+
+def test_default_stream_work_is_waited_for():
+    """A device series still being written by work queued on torch's default
+    (the legacy) stream: a call given no stream runs after that work, as the
+    entry points document."""
+    n = 4000
+    s = synth.ar1(n, 61, 0.9)
+    src = torch.tensor(s, dtype=torch.float64, device="cuda")
+    t = torch.zeros(n, dtype=torch.float64, device="cuda")
+    assert torch.cuda.current_stream().cuda_stream == 0
+    kw = dict(m=3, tau=1, eps=0.5, norm=1, theiler=1)
+    r = gp.RQA(gpu_settings(**kw))
+    for _ in range(2):           # a plain run, then a graph replay
+        t.zero_()
+        big = torch.randn(4096, 4096, device="cuda")
+        for _ in range(12):      # tens of milliseconds of queued work first
+            big = torch.tanh(big @ big)
+        t.copy_(src)
+        meas = r.run(t)
+        _check(r, meas, s, **kw)
