@@ -434,6 +434,17 @@ int Engine::cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? RQA_ENOMEM : RQA_ECUDA;
 }
 
+void Engine::release_arena() {
+  cudaSetDevice(dev_);
+  if (graph_) {  // the captured graph points into the arena
+    cudaGraphExecDestroy(graph_);
+    graph_ = nullptr;
+    graph_key_.clear();
+  }
+  free_arena(own_);
+  cudaStreamSynchronize(own_);
+}
+
 void Engine::free_arena(cudaStream_t st) {
   if (!arena_) return;
   if (pool_)

@@ -117,6 +117,10 @@ class Engine {
   int sm_count() const { return sms_; }
   float last_tile_ms() const { return tile_ms_; }
   float last_total_ms() const { return total_ms_; }
+  // Device arena held between runs, and its release (after the last run on
+  // the engine's own stream has completed; the next run allocates again).
+  size_t arena_bytes() const { return arena_cap_; }
+  void release_arena();
 
  private:
   int run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResult>& results,

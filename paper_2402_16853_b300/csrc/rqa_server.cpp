@@ -104,6 +104,10 @@ void rqa_server::worker(int idx) {
     }
     std::vector<rqa::SeriesResult> res;
     const int rc = eng.run(in, res, nullptr, rqa::Engine::kNoGraph);
+    // the budget bounds the memory of the admitted requests; an engine's
+    // arena outlives its epoch, so one larger than the worker's share of the
+    // budget is released, and the arenas held between epochs stay within it
+    if (eng.arena_bytes() > budget / static_cast<size_t>(workers_n)) eng.release_arena();
     {
       std::lock_guard<std::mutex> lk(mu);
       for (size_t q = 0; q < epoch.size(); ++q) {

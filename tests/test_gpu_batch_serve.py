@@ -147,6 +147,35 @@ def _admission(srv, settings, series):
     assert 0 < peak[0] <= 24 << 20 and 1 <= peak[1] <= 4
 
 
+def test_memory_held_between_epochs_stays_within_budget():
+    """Each worker keeps its device arena from epoch to epoch; one larger than
+    its share of the budget is released, so what the server holds once the
+    stream is done stays within the budget."""
+    import torch
+    torch.zeros(1, device="cuda")
+    settings, series = _mixed(40, 17, lo=20000, hi=60000)
+    budget = 256 << 20
+    srv = gp.Server(budget, max_slots=8)
+    try:
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        ts = [srv.submit(stg, s) for stg, s in zip(settings, series)]
+        got = []
+        for t in ts:
+            rc, m = srv.wait(t, 60_000)
+            assert rc == 0
+            got.append(m)
+        time.sleep(0.2)
+        held = free0 - torch.cuda.mem_get_info()[0]
+        assert held <= budget, (held, budget)
+        for q in (0, 13, 27, 39):   # the same results as single runs
+            r = gp.RQA(settings[q])
+            assert_same_measures(got[q], r.run(series[q]))
+            r.close()
+    finally:
+        srv.close()
+
+
 def test_oversized_request_and_cancel():
     srv = gp.Server(8 << 20, max_slots=1)
     try:
