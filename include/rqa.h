@@ -181,7 +181,10 @@ int rqa_run(rqa_handle* h, const double* host_series, int64_t n);
  * memory (e.g. a torch CUDA tensor), ordered on `cuda_stream` (a
  * cudaStream_t; NULL = the legacy default stream).  The
  * caller keeps the series alive and unmodified until the call returns; the
- * call returns when the results are on the host. */
+ * call returns when the results are on the host.  dev_series must be 8-byte
+ * aligned memory the handle's device can read (its own device memory,
+ * managed memory or mapped pinned host memory); anything else, pageable
+ * host memory included, is refused with RQA_EINVAL before a kernel runs. */
 int rqa_run_device(rqa_handle* h, const double* dev_series, int64_t n,
                    void* cuda_stream);
 
@@ -270,7 +273,9 @@ const char* rqa_last_error(const rqa_handle* h);
  * holds until the process exits; it calls no cudaMalloc/cudaFree.
  *   settings    analysis parameters (validated as by rqa_create)
  *   dev_series  n_points FP64 values in device memory, read on cuda_stream
- *   dev_hist    device buffer of 3 * (n_vec + 1) uint64 that receives the
+ *               (8-byte aligned and readable by the current device, as for
+ *               rqa_run_device; else RQA_EINVAL before anything runs)
+ *   dev_hist    device buffer of 3 * (n_vec + 1) uint64 (8-byte aligned) that receives the
  *               diagonal, vertical and white-vertical histograms, laid out
  *               like rqa_histogram (kind * (n_vec + 1) + length)
  *   cuda_stream cudaStream_t (NULL: legacy default stream); the call returns

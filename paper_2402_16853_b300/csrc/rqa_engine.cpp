@@ -300,6 +300,31 @@ void assign_streams(const std::vector<double>& work, int nside, std::vector<int>
 
 }  // namespace
 
+int check_device_pointer(const void* p, size_t align, int device, const char** what_failed) {
+  if (reinterpret_cast<uintptr_t>(p) % align != 0) {
+    *what_failed = align == 8 ? "device pointer is not 8-byte aligned"
+                              : "device pointer is not 4-byte aligned";
+    return RQA_EINVAL;
+  }
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    *what_failed = "not a pointer CUDA knows";
+    return RQA_EINVAL;
+  }
+  const bool ok = (a.type == cudaMemoryTypeDevice && a.device == device) ||
+                  a.type == cudaMemoryTypeManaged ||
+                  (a.type == cudaMemoryTypeHost && a.devicePointer == p);
+  if (!ok) {
+    *what_failed = a.type == cudaMemoryTypeDevice
+                       ? "device pointer belongs to another device"
+                       : "host memory the device cannot read (pass it to the host entry point)";
+    return RQA_EINVAL;
+  }
+  return RQA_OK;
+}
+
+
 int validate_settings(const rqa_settings* st, std::string* msg) {
   if (!st) {
     *msg = "settings pointer is NULL";
@@ -568,7 +593,12 @@ int Engine::run_impl(const std::vector<SeriesInput>& in, std::vector<SeriesResul
   bool any_fp32 = false;
   for (int q = 0; q < count; ++q) {
     std::string msg;
-    const int s = validate_input(in[q], &msg);
+    int s = validate_input(in[q], &msg);
+    const char* why = nullptr;
+    if (s == RQA_OK && in[q].dev) s = check_device_pointer(in[q].dev, 8, dev_, &why);
+    if (s == RQA_OK && in[q].dev2) s = check_device_pointer(in[q].dev2, 8, dev_, &why);
+    if (s == RQA_OK && in[q].bits_dev) s = check_device_pointer(in[q].bits_dev, 4, dev_, &why);
+    if (why) msg = why;
     if (s != RQA_OK) {
       results[q].status = s;
       if (count == 1) return fail(s, msg);

@@ -10,6 +10,13 @@ namespace rqa {
 
 using TileFn = void (*)(const SeriesDesc*, const Item*, int, int*);
 
+// A caller's device pointer that kernels will read: RQA_OK if it is `align`-
+// byte aligned and CUDA reports memory that `device` can read (its own
+// device memory, managed memory, or mapped pinned host memory), else
+// RQA_EINVAL with *what_failed set to a static description.  A misaligned
+// or host pointer would otherwise fault the device.
+int check_device_pointer(const void* p, size_t align, int device, const char** what_failed);
+
 // Fused tile kernel for embedding dimension m (1..10), norm (0 max, 1 L2,
 // 2 L1), columns per lane `cols` (4), FP64-everywhere or FP32 + recheck, and
 // the symmetric (RQA) or cross-recurrence matrix, with or without row bands.

@@ -153,6 +153,10 @@ extern "C" int rqa_run_noalloc(const rqa_settings* settings, const double* dev_s
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(RQA_ECUDA, cudaGetErrorString(e));
+  const char* why = nullptr;
+  if (check_device_pointer(dev_series, 8, dev, &why) != RQA_OK ||
+      check_device_pointer(dev_hist, 8, dev, &why) != RQA_OK)
+    return fail(RQA_EINVAL, why);
   void* basep = nullptr;
   std::string msg;
   int rc = scratch_base(dev, &basep, &msg);
