@@ -1283,6 +1283,7 @@ int Engine::sample(const int64_t* i, const int64_t* j, int64_t count, uint8_t* o
   if (!last_sd_) return fail(RQA_EINVAL, "no run to sample from");
   if (last_matrix_) return fail(RQA_EINVAL, "a precomputed matrix has no decisions to sample");
   if (count <= 0) return RQA_OK;
+  if (count > (int64_t(1) << 32)) return fail(RQA_EINVAL, "more than 2^32 decisions in one call");
   cudaError_t e = cudaSetDevice(dev_);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   void* buf = nullptr;
