@@ -46,9 +46,13 @@ int plot_common(const rqa_settings* settings, const double* host_x, int64_t nx,
     return plot_fail(RQA_ESHORT, "series shorter than the embedding");
   if (n > RQA_MAX_N || n2 > RQA_MAX_N)
     return plot_fail(RQA_ETOOBIG, "more than RQA_MAX_N embedded vectors");
-  const int64_t wpr = (cols + 31) / 32;
-  const size_t out_bytes = sizeof(uint32_t) * static_cast<size_t>(rows) * wpr;
-  if (out_bytes > (size_t(4) << 30)) return plot_fail(RQA_ETOOBIG, "plot above 4 GiB");
+  // window origin far beyond any matrix, or a plot above 4 GiB (tested by
+  // division, so that no product can wrap)
+  if (i0 > (int64_t(1) << 40) || j0 > (int64_t(1) << 40))
+    return plot_fail(RQA_EINVAL, "window origin beyond 2^40");
+  const int64_t wpr = cols / 32 + (cols % 32 != 0);
+  if (wpr > 0 && rows > (int64_t(1) << 30) / wpr) return plot_fail(RQA_ETOOBIG, "plot above 4 GiB");
+  const size_t out_bytes = sizeof(uint32_t) * static_cast<size_t>(rows) * static_cast<size_t>(wpr);
   if (rows == 0 || cols == 0) return RQA_OK;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -123,3 +123,25 @@ def test_tuning_table_files(tmp_path):
         assert lib.rqa_autotune_load(R.TUNING_TABLE.encode(), ctypes.byref(cnt)) == 0
         assert cnt.value > 0
         lib.rqa_autotune_clear()
+
+
+def test_plot_window_limits_checked_on_the_host():
+    """Windows whose byte size or origin would overflow are refused before any
+    device work (so this runs without a GPU): rows x words above 4 GiB, a
+    row count whose product with the words per row wraps, an origin past 2^40."""
+    import ctypes
+    import numpy as np
+    from paper_2402_16853_b300.rqa import _cs
+    lib = rqa_pkg.load()
+    cs = _cs(rqa_pkg.Settings(m=2, tau=1, eps=0.5))
+    s = np.linspace(0.0, 1.0, 100)
+    ps = s.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    out = (ctypes.c_uint32 * 4)()
+    cases = [((0, 0, 1 << 20, 1 << 20), 9),          # 128 GiB of plot
+             ((0, 0, 1 << 62, 32), 9),                # 4 * rows * 1 word wraps to 0
+             ((0, 0, 1 << 40, (1 << 63) - 1), 9),     # cols near INT64_MAX
+             ((1 << 41, 0, 4, 4), 1), ((0, 1 << 50, 4, 4), 1),
+             ((-1, 0, 4, 4), 1)]
+    for (i0, j0, rows, cols), want in cases:
+        rc = lib.rqa_recurrence_plot(ctypes.byref(cs), ps, len(s), i0, j0, rows, cols, out)
+        assert rc == want, (i0, j0, rows, cols, rc)
