@@ -483,11 +483,10 @@ __device__ __forceinline__ uint32_t live_mask(int j, int r0, int n, int w) {
 }
 
 // Row buffer layout: FP32 rows hold each coordinate twice (x0 x0 x1 x1 ...)
-// for the packed L2 and L-infinity paths, once for L1; FP64 rows hold m
-// doubles.
+// for the packed paths (every norm); FP64 rows hold m doubles.
 template <int M, int NORM, bool F64>
 __host__ __device__ constexpr int tile_row_elems() {
-  return F64 ? M : (NORM != 2 ? ((2 * M + 3) / 4) * 4 : ((M + 3) / 4) * 4);
+  return F64 ? M : ((2 * M + 3) / 4) * 4;
 }
 
 // Shared-memory bytes of the tile kernel for a launch shape.
@@ -512,7 +511,10 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
   static_assert(C <= 4, "the short-run counters are flushed for at most 8 two-colour words a block");
   using T = typename std::conditional<F64, double, float>::type;
   constexpr int RE = tile_row_elems<M, NORM, F64>();
-  constexpr bool PACKED = !F64 && NORM != 2 && (C % 2 == 0);  // L2 and L-infinity
+  constexpr bool PACKED = !F64 && (C % 2 == 0);  // two columns per packed operation
+  // the packed L2 and L-infinity margins are negated (sign bit 1 = recurrent),
+  // the packed L1 one and the scalar ones are not (sign bit 1 = no recurrence)
+  constexpr bool SIGN_REC = PACKED && NORM != 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NW = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5;
@@ -664,21 +666,16 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           const int i = r0 + lane;
           if constexpr (!F64) {
             // 16-byte loads of the padded FP32 vector (mp is a multiple of 4)
-            // and 16-byte stores; the L2 layout holds each coordinate twice.
+            // and 16-byte stores; the layout holds each coordinate twice.
             // Slots past the m coordinates are never read.
             const float4* src = reinterpret_cast<const float4*>(xe + (int64_t)i * mp);
             float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(rowbuf) + lane * RE);
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if constexpr (NORM != 2) {
 #pragma unroll
-              for (int p = 0; p < (RE / 4 + 1) / 2; ++p) {
-                const float4 v = i < n ? src[p] : z4;
-                dst[2 * p] = make_float4(v.x, v.x, v.y, v.y);
-                if (2 * p + 1 < RE / 4) dst[2 * p + 1] = make_float4(v.z, v.z, v.w, v.w);
-              }
-            } else {
-#pragma unroll
-              for (int p = 0; p < RE / 4; ++p) dst[p] = i < n ? src[p] : z4;
+            for (int p = 0; p < (RE / 4 + 1) / 2; ++p) {
+              const float4 v = i < n ? src[p] : z4;
+              dst[2 * p] = make_float4(v.x, v.x, v.y, v.y);
+              if (2 * p + 1 < RE / 4) dst[2 * p + 1] = make_float4(v.z, v.z, v.w, v.w);
             }
           } else {
 #pragma unroll
@@ -757,6 +754,37 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             }
 #pragma unroll
             for (int c = 0; c < C / 2; ++c) mn[2 * c + 1] = mn[2 * c];
+          } else if constexpr (PACKED && NORM == 2) {
+            // L1, two columns per packed subtraction, then thr minus each |d_k|
+            // in pair_margin()'s order (x_r + (-x_c) rounds exactly as
+            // x_r - x_c), so every margin is the scalar one; its sign bit is 1
+            // for a pair that does not recur.
+#pragma unroll 4
+            for (int t = 31; t >= 0; --t) {
+              float2 xr2[2 * (RE / 4)];
+              const float4* rb = reinterpret_cast<const float4*>(rowbuf) + t * (RE / 4);
+#pragma unroll
+              for (int p = 0; p < RE / 4; ++p) {  // 16-byte loads: two coordinates each
+                const float4 v = rb[p];
+                xr2[2 * p] = make_float2(v.x, v.y);
+                xr2[2 * p + 1] = make_float2(v.z, v.w);
+              }
+#pragma unroll
+              for (int c = 0; c < C / 2; ++c) {
+                float a0 = thr, a1 = thr;
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                  const float2 dd = __fadd2_rn(xr2[k], xn2[c][k]);
+                  a0 = __fsub_rn(a0, fabsf(dd.x));
+                  a1 = __fsub_rn(a1, fabsf(dd.y));
+                }
+                Nw[2 * c] = __funnelshift_l(__float_as_uint(a0), Nw[2 * c], 1);
+                Nw[2 * c + 1] = __funnelshift_l(__float_as_uint(a1), Nw[2 * c + 1], 1);
+                mn[2 * c] = fminf(mn[2 * c], fminf(fabsf(a0), fabsf(a1)));
+              }
+            }
+#pragma unroll
+            for (int c = 0; c < C / 2; ++c) mn[2 * c + 1] = mn[2 * c];
           } else if constexpr (PACKED) {
             // L-infinity, two columns per packed subtraction: the exact
             // maximum of |d_k| per column, then mx - thr, the exact negation
@@ -796,7 +824,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
               float xr[M];
               const float* rb = reinterpret_cast<const float*>(rowbuf) + t * RE;
 #pragma unroll
-              for (int k = 0; k < M; ++k) xr[k] = rb[k];
+              for (int k = 0; k < M; ++k) xr[k] = rb[2 * k];
 #pragma unroll
               for (int c = 0; c < C; ++c) {
                 const float acc = pair_margin<M, NORM>(xr, (const float*)xc[c], thr);
@@ -809,8 +837,8 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           for (int c = 0; c < C; ++c) {
             const int j = jw0 + 32 * c + lane;
             const uint32_t live = live_mask<XR>(j, r0, n, wtheiler);
-            // packed: sign bit = recurrent; scalar: sign bit = not recurrent
-            uint32_t R = (PACKED ? Nw[c] : ~Nw[c]) & live;
+            // packed L2 / L-infinity: sign bit = recurrent; else not recurrent
+            uint32_t R = (SIGN_REC ? Nw[c] : ~Nw[c]) & live;
             if (mn[c] <= band && live) {
               // near-radius pairs: re-decide in FP64 with the exact order
               uint32_t todo = live;
@@ -821,7 +849,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
                 const float* rb = reinterpret_cast<const float*>(rowbuf) + t * RE;
 #pragma unroll
                 for (int k = 0; k < M; ++k) {
-                  xr[k] = PACKED ? rb[2 * k] : rb[k];
+                  xr[k] = rb[2 * k];
                   if constexpr (PACKED) {
                     xcc[k] = -((c % 2) ? xn2[c / 2][k].y : xn2[c / 2][k].x);
                   } else {
