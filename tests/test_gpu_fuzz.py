@@ -1,7 +1,12 @@
 """Seeded random sweep: RQA, cross recurrence and matrix input on random
 sizes, embeddings, norms, radii, Theiler windows, strip widths and row-band
 heights, each against the oracle bit for bit.  Sizes stay small enough for
-the materialised oracle; the draws cover ragged tails on both axes."""
+the materialised oracle; the draws cover ragged tails on both axes.  Odd
+cases run two columns per lane, even ones four.  RQA_FUZZ_CASES sets the
+number of RQA cases (40; half as many cross and matrix cases) for a longer
+sweep."""
+import os
+
 import numpy as np
 import pytest
 
@@ -13,7 +18,7 @@ import paper_2402_16853_b300 as gp
 
 pytestmark = pytest.mark.gpu
 
-CASES = 40
+CASES = int(os.environ.get("RQA_FUZZ_CASES", "40"))
 
 
 def _series(rng, N):
@@ -28,7 +33,8 @@ def _series(rng, N):
     return synth.dyadic(N, seed, levels=int(rng.integers(2, 9)), scale_log2=-2)
 
 
-def _env(monkeypatch, rng):
+def _env(monkeypatch, rng, case):
+    monkeypatch.setenv("RQA_TILE_COLS", "2" if case % 2 else "4")
     monkeypatch.setenv("RQA_TILE_WARPS", str(int(rng.integers(1, 9))))
     rows = int(rng.choice([0, 32, 64, 96, 256, 1024]))
     monkeypatch.setenv("RQA_BAND_ROWS", str(rows))
@@ -54,7 +60,7 @@ def _compare(r, meas, want):
 @pytest.mark.parametrize("case", range(CASES))
 def test_random_rqa(monkeypatch, case):
     rng = np.random.default_rng(5000 + case)
-    _env(monkeypatch, rng)
+    _env(monkeypatch, rng, case)
     s = _series(rng, int(rng.integers(20, 2600)))
     kw = _settings(rng, float(np.std(s)) or 1.0)
     if len(s) - (kw["m"] - 1) * kw["tau"] < 1:
@@ -67,7 +73,7 @@ def test_random_rqa(monkeypatch, case):
 @pytest.mark.parametrize("case", range(CASES // 2))
 def test_random_cross(monkeypatch, case):
     rng = np.random.default_rng(6000 + case)
-    _env(monkeypatch, rng)
+    _env(monkeypatch, rng, case)
     x = _series(rng, int(rng.integers(20, 2200)))
     y = _series(rng, int(rng.integers(20, 2200)))
     kw = _settings(rng, float(np.std(np.concatenate([x, y]))) or 1.0)
@@ -82,7 +88,7 @@ def test_random_cross(monkeypatch, case):
 @pytest.mark.parametrize("case", range(CASES // 2))
 def test_random_matrix(monkeypatch, case):
     rng = np.random.default_rng(7000 + case)
-    _env(monkeypatch, rng)
+    _env(monkeypatch, rng, case)
     rows, cols = (int(v) for v in rng.integers(1, 2100, 2))
     R = (rng.random((rows, cols)) < float(rng.uniform(0.02, 0.98))).astype(np.uint8)
     w = int(rng.choice([0, 1, 3]))
