@@ -95,3 +95,23 @@ def test_random_matrix(monkeypatch, case):
     want = oracle.matrix_rqa(R, oracle.Settings(m=1, tau=1, eps=1.0, norm=0, theiler=w))
     r = gp.RQA(gpu_settings(1, 1, 1.0, 0, w))
     _compare(r, r.run_matrix(R), want)
+
+
+MID_CASES = int(os.environ.get("RQA_FUZZ_MID_CASES", "4"))
+
+
+@pytest.mark.parametrize("case", range(MID_CASES))
+def test_random_rqa_mid_size(monkeypatch, case):
+    """Longer series (5,000-30,000 points) against the streaming oracle:
+    many blocks right of the diagonal, long white runs, row bands chosen by
+    the library or forced."""
+    rng = np.random.default_rng(8000 + case)
+    monkeypatch.setenv("RQA_TILE_COLS", "2" if case % 2 else "4")
+    monkeypatch.setenv("RQA_TILE_WARPS", str(int(rng.choice([1, 2, 4, 8]))))
+    if rng.random() < 0.5:
+        monkeypatch.setenv("RQA_BAND_ROWS", str(int(rng.choice([0, 256, 1024, 4096]))))
+    s = _series(rng, int(rng.integers(5000, 30000)))
+    kw = _settings(rng, float(np.std(s)) or 1.0)
+    want = oracle.rqa(s, oracle.Settings(**kw), mode="streaming")
+    r = gp.RQA(gpu_settings(**kw))
+    _compare(r, r.run(s), want)
