@@ -935,6 +935,36 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             else
               D = transpose32(D, lane);
           }
+          if constexpr (XR && !MX) {
+            // cross recurrence, a block below the top row block with no
+            // column left of the matrix: every column word is full
+            if (r0 + 32 <= n && col0 >= 0) {
+              auto emit2 = [&](uint32_t col, uint32_t len) { hs.add2(col, len); };
+              cst_s[c * 32 + lane] = scan2_full(
+                  R, cst_s[c * 32 + lane], sc, hs, emit2, [&](uint32_t col, uint32_t len) {
+                    if (banded && R1 < n)  // touches the band's bottom edge: join later
+                      colfirst[j] = len | (col << 31);
+                    else if (len)
+                      hs.add2(col, len);
+                  });
+              const int k = col0 - r0 + d;
+              auto emitd = [&](uint32_t len) { hs.add(HIST_DIAG, len); };
+              auto firstd = [&](uint32_t len) {
+                if (k >= klo) dia_a[off + k - klo] = (uint16_t)len;
+              };
+              if (c == C - 1) {
+                dU_new[c * 32 + lane] =
+                    scanb_full(D | segL, dL, sc, hs, emitd, firstd) - (uint32_t)d;
+              } else {
+                const uint32_t w = (Dprev & segL) | (D & segU);
+                dU_new[c * 32 + lane] = scanb_full(__funnelshift_r(w, w, d),
+                                                   dU_old[(c + 1) * 32 + lane], sc, hs, emitd, firstd);
+              }
+              Dprev = D;
+              hs.drain(lane);
+              continue;
+            }
+          }
           if constexpr (!XR && !MX) {
             // two or more blocks right of the diagonal (almost every
             // sub-block): every column and row word is full, no row ends
