@@ -428,41 +428,56 @@ __global__ void merge_cols_kernel(SeriesDesc* __restrict__ sd) {
       ocol = zb >> 31;
       olen = zb & LEN;
     }
-    for (int64_t g = gb - 1; g >= 0; --g) {
-      const uint32_t z = S.col_z[g * n + j];
-      if (z & WHOLE) {
-        const uint32_t zc = z >> 31;
-        const uint64_t zl = z & LEN;
-        if (loi_open) {
-          if (loi_col == zc) {
-            loi_len += zl;
+    // the bands' descriptors read MERGE_AHEAD at a time (their addresses
+    // follow from g alone, so the loads need not wait on each other), then
+    // joined in order
+    for (int64_t g0 = gb - 1; g0 >= 0; g0 -= MERGE_AHEAD) {
+      uint32_t zs[MERGE_AHEAD], as[MERGE_AHEAD];
+#pragma unroll
+      for (int v = 0; v < MERGE_AHEAD; ++v) {
+        const int64_t gv = g0 - v;
+        zs[v] = gv >= 0 ? S.col_z[gv * n + j] : 0u;
+        as[v] = gv >= 0 ? S.col_a[gv * n + j] : 0u;
+      }
+#pragma unroll
+      for (int v = 0; v < MERGE_AHEAD; ++v) {
+        const int64_t g = g0 - v;
+        if (g < 0) break;
+        const uint32_t z = zs[v];
+        if (z & WHOLE) {
+          const uint32_t zc = z >> 31;
+          const uint64_t zl = z & LEN;
+          if (loi_open) {
+            if (loi_col == zc) {
+              loi_len += zl;
+            } else {
+              loi_open = false;
+              ocol = zc;
+              olen = zl;
+            }
+          } else if (olen && ocol == zc) {
+            olen += zl;
           } else {
-            loi_open = false;
+            emit2(h, S, ocol, olen);
             ocol = zc;
             olen = zl;
           }
-        } else if (olen && ocol == zc) {
-          olen += zl;
         } else {
-          emit2(h, S, ocol, olen);
-          ocol = zc;
-          olen = zl;
+          const uint32_t a = as[v];
+          const uint32_t ac = a >> 31;
+          const uint64_t al = a & 0x7FFFFFFFu;
+          if (loi_open) {
+            if (loi_col == ac) loi_len += al; else emit2(h, S, ac, al);
+            loi_open = false;
+          } else if (olen && ocol == ac) {
+            emit2(h, S, ocol, olen + al);
+          } else {
+            emit2(h, S, ocol, olen);
+            emit2(h, S, ac, al);
+          }
+          ocol = z >> 31;
+          olen = g > 0 ? (z & LEN) : 0;  // band 0 closed its own top run
         }
-      } else {
-        const uint32_t a = S.col_a[g * n + j];
-        const uint32_t ac = a >> 31;
-        const uint64_t al = a & 0x7FFFFFFFu;
-        if (loi_open) {
-          if (loi_col == ac) loi_len += al; else emit2(h, S, ac, al);
-          loi_open = false;
-        } else if (olen && ocol == ac) {
-          emit2(h, S, ocol, olen + al);
-        } else {
-          emit2(h, S, ocol, olen);
-          emit2(h, S, ac, al);
-        }
-        ocol = z >> 31;
-        olen = g > 0 ? (z & LEN) : 0;  // band 0 closed its own top run
       }
     }
     emit2(h, S, ocol, olen);  // the open run touching row 0
