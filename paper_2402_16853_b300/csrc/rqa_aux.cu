@@ -552,28 +552,40 @@ __global__ void merge_cross_cols_kernel(SeriesDesc* __restrict__ sd) {
     const uint32_t zl = S.col_z[(nb - 1) * n2 + j];
     uint32_t ocol = zl >> 31;
     uint64_t olen = zl & LEN;
-    for (int64_t g = nb - 2; g >= 0; --g) {
-      const uint32_t z = S.col_z[g * n2 + j];
-      if (z & WHOLE) {
-        if (olen && ocol == (z >> 31)) {
-          olen += z & LEN;
+    for (int64_t g0 = nb - 2; g0 >= 0; g0 -= MERGE_AHEAD) {  // eight bands' loads at a time
+      uint32_t zs[MERGE_AHEAD], as[MERGE_AHEAD];
+#pragma unroll
+      for (int v = 0; v < MERGE_AHEAD; ++v) {
+        const int64_t gv = g0 - v;
+        zs[v] = gv >= 0 ? S.col_z[gv * n2 + j] : 0u;
+        as[v] = gv >= 0 ? S.col_a[gv * n2 + j] : 0u;
+      }
+#pragma unroll
+      for (int v = 0; v < MERGE_AHEAD; ++v) {
+        const int64_t g = g0 - v;
+        if (g < 0) break;
+        const uint32_t z = zs[v];
+        if (z & WHOLE) {
+          if (olen && ocol == (z >> 31)) {
+            olen += z & LEN;
+          } else {
+            emit2(h, S, ocol, olen);
+            ocol = z >> 31;
+            olen = z & LEN;
+          }
         } else {
-          emit2(h, S, ocol, olen);
+          const uint32_t a = as[v];
+          const uint32_t ac = a >> 31;
+          const uint64_t al = a & 0x7FFFFFFFu;
+          if (olen && ocol == ac) {
+            emit2(h, S, ocol, olen + al);
+          } else {
+            emit2(h, S, ocol, olen);
+            emit2(h, S, ac, al);
+          }
           ocol = z >> 31;
-          olen = z & LEN;
+          olen = g > 0 ? (z & LEN) : 0;  // band 0 closed its own top run
         }
-      } else {
-        const uint32_t a = S.col_a[g * n2 + j];
-        const uint32_t ac = a >> 31;
-        const uint64_t al = a & 0x7FFFFFFFu;
-        if (olen && ocol == ac) {
-          emit2(h, S, ocol, olen + al);
-        } else {
-          emit2(h, S, ocol, olen);
-          emit2(h, S, ac, al);
-        }
-        ocol = z >> 31;
-        olen = g > 0 ? (z & LEN) : 0;  // band 0 closed its own top run
       }
     }
     emit2(h, S, ocol, olen);
