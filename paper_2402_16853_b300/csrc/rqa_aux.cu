@@ -210,7 +210,7 @@ constexpr int MERGE_AHEAD = 8;
 // at once).  A row or diagonal that continues past the group's left edge
 // leaves its open run in rcarry / dcarry, and the next group starts from it;
 // the descriptors of strip Q sit at strip_offset(Q) - strip_offset(q0).
-__global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd, int64_t q0, int64_t q1) {
+__device__ void merge_rows_body(SeriesDesc* __restrict__ sd, int64_t q0, int64_t q1) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || S.cross) return;
   __shared__ uint32_t sh[3 * HB];
@@ -286,7 +286,7 @@ __global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd, int64_t q0, int64
 // Each item left the black run touching the diagonal's entry (a), the black
 // run touching its exit (z), or an all-black flag.  With one band the items
 // are the strips, Q = 0 .. (n-1-k)/sw.
-__global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd, int64_t q0, int64_t q1) {
+__device__ void merge_diags_body(SeriesDesc* __restrict__ sd, int64_t q0, int64_t q1) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || S.cross) return;
   __shared__ uint32_t sh[3 * HB];
@@ -397,7 +397,7 @@ __global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd, int64_t q0, int6
 // closed its top run itself unless it is one run or touches row j-1.  Join
 // them bottom-up; the final run touching row j-1 goes to colend for the
 // line-of-identity join.
-__global__ void merge_cols_kernel(SeriesDesc* __restrict__ sd) {
+__device__ void merge_cols_body(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || S.cross || S.nbands <= 1) return;
   __shared__ uint32_t sh[3 * HB];
@@ -494,7 +494,7 @@ __global__ void merge_cols_kernel(SeriesDesc* __restrict__ sd) {
 // all rows); the diagonal leaves an item at row max(R0, J0 - k).  The
 // descriptors mean what they mean for RQA; runs touching the matrix border
 // were closed in the tile kernel or are closed here at the diagonal's ends.
-__global__ void merge_cross_diags_kernel(SeriesDesc* __restrict__ sd) {
+__device__ void merge_cross_diags_body(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || !S.cross) return;
   __shared__ uint32_t sh[3 * HB];
@@ -539,7 +539,7 @@ __global__ void merge_cross_diags_kernel(SeriesDesc* __restrict__ sd) {
 // holds its first run (col_a, touching its bottom edge) unless the column's
 // segment there is one run, and every band but 0 its top run (col_z, with a
 // whole-segment flag; band 0 records it only when whole).  Join bottom-up.
-__global__ void merge_cross_cols_kernel(SeriesDesc* __restrict__ sd) {
+__device__ void merge_cross_cols_body(SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || !S.cross || S.nbands <= 1) return;
   __shared__ uint32_t sh[3 * HB];
@@ -591,6 +591,39 @@ __global__ void merge_cross_cols_kernel(SeriesDesc* __restrict__ sd) {
     emit2(h, S, ocol, olen);
   }
   h.flush(S);
+}
+
+// The merges as kernels of their own (strip groups walk rows and diagonals
+// group by group), and fused: the walks of one series touch disjoint
+// outputs (rowend, colend) and add to the histograms by atomics, so they need
+// no order among themselves, and one launch (blockIdx.z: the walk) lets their
+// latency-bound loads overlap.
+__global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd, int64_t q0, int64_t q1) {
+  merge_rows_body(sd, q0, q1);
+}
+__global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd, int64_t q0, int64_t q1) {
+  merge_diags_body(sd, q0, q1);
+}
+__global__ void merge_cols_kernel(SeriesDesc* __restrict__ sd) { merge_cols_body(sd); }
+__global__ void merge_cross_diags_kernel(SeriesDesc* __restrict__ sd) {
+  merge_cross_diags_body(sd);
+}
+__global__ void merge_cross_cols_kernel(SeriesDesc* __restrict__ sd) { merge_cross_cols_body(sd); }
+// z = 0 rows, 1 diagonals, 2 columns (row bands only)
+__global__ void merge_sym_kernel(SeriesDesc* __restrict__ sd) {
+  if (blockIdx.z == 0)
+    merge_rows_body(sd, 0, -1);
+  else if (blockIdx.z == 1)
+    merge_diags_body(sd, 0, -1);
+  else
+    merge_cols_body(sd);
+}
+// z = 0 diagonals, 1 columns (row bands only)
+__global__ void merge_cross_kernel(SeriesDesc* __restrict__ sd) {
+  if (blockIdx.z == 0)
+    merge_cross_diags_body(sd);
+  else
+    merge_cross_cols_body(sd);
 }
 
 // ----------------------------------------------------------------- finalize
@@ -894,6 +927,8 @@ int preload_aux_kernels() {
       reinterpret_cast<const void*>(merge_cols_kernel),
       reinterpret_cast<const void*>(merge_cross_diags_kernel),
       reinterpret_cast<const void*>(merge_cross_cols_kernel),
+      reinterpret_cast<const void*>(merge_sym_kernel),
+      reinterpret_cast<const void*>(merge_cross_kernel),
       reinterpret_cast<const void*>(join_loi_kernel),
       reinterpret_cast<const void*>(diag_full_kernel),
       reinterpret_cast<const void*>(last_bin_kernel),
@@ -920,27 +955,21 @@ int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cro
   if (blocks > 4 * sms) blocks = 4 * sms;
   if (blocks < 1) blocks = 1;
   int launched = 0;
-  if (sym && !grouped) {
-    merge_rows_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd, 0, -1);
-    merge_diags_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd, 0, -1);
-    launched += 2;
+  if (sym && !grouped) {  // rows, diagonals and (bands) columns in one launch
+    merge_sym_kernel<<<dim3((unsigned)blocks, count, bands ? 3 : 2), 256, 0, st>>>(d_sd);
+    ++launched;
+  } else if (sym && bands) {  // strip groups merged rows and diagonals already
+    merge_cols_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+    ++launched;
   }
   if (sym) {
-    if (bands) {
-      merge_cols_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
-      ++launched;
-    }
     join_loi_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
     diag_full_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
     launched += 2;
   }
-  if (cross) {
-    merge_cross_diags_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
-    launched += 1;
-    if (bands) {
-      merge_cross_cols_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
-      ++launched;
-    }
+  if (cross) {  // diagonals and (bands) columns in one launch
+    merge_cross_kernel<<<dim3((unsigned)blocks, count, bands ? 2 : 1), 256, 0, st>>>(d_sd);
+    ++launched;
   }
   // after every histogram update: the last non-zero bins (the merges above
   // add the lines that cross strip borders)

@@ -234,13 +234,13 @@ def test_served_banded_requests_equal_alone():
 def test_preload_kernels_once_per_process():
     """Every tile kernel instantiation (m = 1..10, three norms, FP32 and FP64,
     RQA and cross, with and without row bands, at four columns per lane, the
-    FP32 ones also at two, and the two matrix-input ones), the eleven
+    FP32 ones also at two, and the two matrix-input ones), the thirteen
     preparation and merge kernels and the set-up kernel of the
     allocation-free entry point (whose static scratch address is resolved at
     the same time) are loaded; a second call finds them loaded and reports
     the same count."""
     n = gp.preload_kernels()
-    assert n == 10 * 3 * 2 * 2 * 2 + 10 * 3 * 2 * 2 + 2 + 11 + 1
+    assert n == 10 * 3 * 2 * 2 * 2 + 10 * 3 * 2 * 2 + 2 + 13 + 1
     assert gp.preload_kernels() == n
     # a run afterwards is unaffected
     s = synth.ar1(600, 5, 0.9)
