@@ -210,10 +210,9 @@ constexpr int MERGE_AHEAD = 8;
 // at once).  A row or diagonal that continues past the group's left edge
 // leaves its open run in rcarry / dcarry, and the next group starts from it;
 // the descriptors of strip Q sit at strip_offset(Q) - strip_offset(q0).
-__device__ void merge_rows_body(SeriesDesc* __restrict__ sd, int64_t q0, int64_t q1) {
+__device__ void merge_rows_body(uint32_t* sh, SeriesDesc* __restrict__ sd, int64_t q0, int64_t q1) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || S.cross) return;
-  __shared__ uint32_t sh[3 * HB];
   BlockHist h{sh};
   h.init();
   const int64_t n = S.n, sw = S.sw;
@@ -286,10 +285,9 @@ __device__ void merge_rows_body(SeriesDesc* __restrict__ sd, int64_t q0, int64_t
 // Each item left the black run touching the diagonal's entry (a), the black
 // run touching its exit (z), or an all-black flag.  With one band the items
 // are the strips, Q = 0 .. (n-1-k)/sw.
-__device__ void merge_diags_body(SeriesDesc* __restrict__ sd, int64_t q0, int64_t q1) {
+__device__ void merge_diags_body(uint32_t* sh, SeriesDesc* __restrict__ sd, int64_t q0, int64_t q1) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || S.cross) return;
-  __shared__ uint32_t sh[3 * HB];
   BlockHist h{sh};
   h.init();
   const int64_t n = S.n, sw = S.sw;
@@ -397,10 +395,9 @@ __device__ void merge_diags_body(SeriesDesc* __restrict__ sd, int64_t q0, int64_
 // closed its top run itself unless it is one run or touches row j-1.  Join
 // them bottom-up; the final run touching row j-1 goes to colend for the
 // line-of-identity join.
-__device__ void merge_cols_body(SeriesDesc* __restrict__ sd) {
+__device__ void merge_cols_body(uint32_t* sh, SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || S.cross || S.nbands <= 1) return;
-  __shared__ uint32_t sh[3 * HB];
   BlockHist h{sh};
   h.init();
   const int64_t n = S.n, H = S.band_h;
@@ -494,10 +491,9 @@ __device__ void merge_cols_body(SeriesDesc* __restrict__ sd) {
 // all rows); the diagonal leaves an item at row max(R0, J0 - k).  The
 // descriptors mean what they mean for RQA; runs touching the matrix border
 // were closed in the tile kernel or are closed here at the diagonal's ends.
-__device__ void merge_cross_diags_body(SeriesDesc* __restrict__ sd) {
+__device__ void merge_cross_diags_body(uint32_t* sh, SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || !S.cross) return;
-  __shared__ uint32_t sh[3 * HB];
   BlockHist h{sh};
   h.init();
   const int64_t n1 = S.n, n2 = S.n2, sw = S.sw, nd = cross_strip_diags(n1, sw);
@@ -539,10 +535,9 @@ __device__ void merge_cross_diags_body(SeriesDesc* __restrict__ sd) {
 // holds its first run (col_a, touching its bottom edge) unless the column's
 // segment there is one run, and every band but 0 its top run (col_z, with a
 // whole-segment flag; band 0 records it only when whole).  Join bottom-up.
-__device__ void merge_cross_cols_body(SeriesDesc* __restrict__ sd) {
+__device__ void merge_cross_cols_body(uint32_t* sh, SeriesDesc* __restrict__ sd) {
   const SeriesDesc& S = sd[blockIdx.y];
   if (S.n <= 0 || !S.hist || !S.cross || S.nbands <= 1) return;
-  __shared__ uint32_t sh[3 * HB];
   BlockHist h{sh};
   h.init();
   const int64_t n2 = S.n2, nb = S.nbands;
@@ -598,32 +593,46 @@ __device__ void merge_cross_cols_body(SeriesDesc* __restrict__ sd) {
 // outputs (rowend, colend) and add to the histograms by atomics, so they need
 // no order among themselves, and one launch (blockIdx.z: the walk) lets their
 // latency-bound loads overlap.
+// (Every body takes the block's shared bins from its kernel, so that the
+// fused kernels hold one set, not one per walk: the walks are latency-bound
+// and need the occupancy.)
 __global__ void merge_rows_kernel(SeriesDesc* __restrict__ sd, int64_t q0, int64_t q1) {
-  merge_rows_body(sd, q0, q1);
+  __shared__ uint32_t sh[3 * HB];
+  merge_rows_body(sh, sd, q0, q1);
 }
 __global__ void merge_diags_kernel(SeriesDesc* __restrict__ sd, int64_t q0, int64_t q1) {
-  merge_diags_body(sd, q0, q1);
+  __shared__ uint32_t sh[3 * HB];
+  merge_diags_body(sh, sd, q0, q1);
 }
-__global__ void merge_cols_kernel(SeriesDesc* __restrict__ sd) { merge_cols_body(sd); }
+__global__ void merge_cols_kernel(SeriesDesc* __restrict__ sd) {
+  __shared__ uint32_t sh[3 * HB];
+  merge_cols_body(sh, sd);
+}
 __global__ void merge_cross_diags_kernel(SeriesDesc* __restrict__ sd) {
-  merge_cross_diags_body(sd);
+  __shared__ uint32_t sh[3 * HB];
+  merge_cross_diags_body(sh, sd);
 }
-__global__ void merge_cross_cols_kernel(SeriesDesc* __restrict__ sd) { merge_cross_cols_body(sd); }
+__global__ void merge_cross_cols_kernel(SeriesDesc* __restrict__ sd) {
+  __shared__ uint32_t sh[3 * HB];
+  merge_cross_cols_body(sh, sd);
+}
 // z = 0 rows, 1 diagonals, 2 columns (row bands only)
 __global__ void merge_sym_kernel(SeriesDesc* __restrict__ sd) {
+  __shared__ uint32_t sh[3 * HB];
   if (blockIdx.z == 0)
-    merge_rows_body(sd, 0, -1);
+    merge_rows_body(sh, sd, 0, -1);
   else if (blockIdx.z == 1)
-    merge_diags_body(sd, 0, -1);
+    merge_diags_body(sh, sd, 0, -1);
   else
-    merge_cols_body(sd);
+    merge_cols_body(sh, sd);
 }
 // z = 0 diagonals, 1 columns (row bands only)
 __global__ void merge_cross_kernel(SeriesDesc* __restrict__ sd) {
+  __shared__ uint32_t sh[3 * HB];
   if (blockIdx.z == 0)
-    merge_cross_diags_body(sd);
+    merge_cross_diags_body(sh, sd);
   else
-    merge_cross_cols_body(sd);
+    merge_cross_cols_body(sh, sd);
 }
 
 // ----------------------------------------------------------------- finalize
@@ -955,21 +964,42 @@ int launch_merges(SeriesDesc* d_sd, int count, int64_t max_n, bool sym, bool cro
   if (blocks > 4 * sms) blocks = 4 * sms;
   if (blocks < 1) blocks = 1;
   int launched = 0;
-  if (sym && !grouped) {  // rows, diagonals and (bands) columns in one launch
+  // Small sets: rows, diagonals and (bands) columns in one launch, their
+  // latency-bound walks overlapping (2,000 points: 0.134 -> 0.112 ms per
+  // run).  Separate launches from 2^17 vectors on (1M points: 4.5 against
+  // 6.1 ms, the concurrent walks over gigabytes of descriptors in each
+  // other's way) and for sets of many series (the 4,096-series batch: 309
+  // against 314 ms of device time).
+  const bool fuse = max_n <= (int64_t(1) << 17) && count <= 8;
+  if (sym && !grouped && fuse) {
     merge_sym_kernel<<<dim3((unsigned)blocks, count, bands ? 3 : 2), 256, 0, st>>>(d_sd);
     ++launched;
-  } else if (sym && bands) {  // strip groups merged rows and diagonals already
-    merge_cols_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
-    ++launched;
+  } else {
+    if (sym && !grouped) {
+      merge_rows_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd, 0, -1);
+      merge_diags_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd, 0, -1);
+      launched += 2;
+    }
+    if (sym && bands) {  // (strip groups merged their rows and diagonals already)
+      merge_cols_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+      ++launched;
+    }
   }
   if (sym) {
     join_loi_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
     diag_full_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
     launched += 2;
   }
-  if (cross) {  // diagonals and (bands) columns in one launch
+  if (cross && fuse) {  // diagonals and (bands) columns in one launch
     merge_cross_kernel<<<dim3((unsigned)blocks, count, bands ? 2 : 1), 256, 0, st>>>(d_sd);
     ++launched;
+  } else if (cross) {
+    merge_cross_diags_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+    ++launched;
+    if (bands) {
+      merge_cross_cols_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(d_sd);
+      ++launched;
+    }
   }
   // after every histogram update: the last non-zero bins (the merges above
   // add the lines that cross strip borders)
