@@ -184,7 +184,12 @@ int rqa_run(rqa_handle* h, const double* host_series, int64_t n);
  * call returns when the results are on the host.  dev_series must be 8-byte
  * aligned memory the handle's device can read (its own device memory,
  * managed memory or mapped pinned host memory); anything else, pageable
- * host memory included, is refused with RQA_EINVAL before a kernel runs. */
+ * host memory included, is refused with RQA_EINVAL before a kernel runs.
+ * The call waits for its results, so it must not be issued on a stream that
+ * is being captured into a CUDA graph; from the second consecutive call with
+ * the same series length, pointer and stream the library replays a graph of
+ * its own, and the series' values, like the settings', are read anew by
+ * every call. */
 int rqa_run_device(rqa_handle* h, const double* dev_series, int64_t n,
                    void* cuda_stream);
 
