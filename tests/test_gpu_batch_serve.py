@@ -2,6 +2,7 @@
 every request of a served mix, must equal the FP64 oracle (and hence its own
 single-series run) exactly; admission must queue under a small memory
 budget and never exceed it; queued requests can be cancelled."""
+import os
 import threading
 import time
 
@@ -324,4 +325,38 @@ def test_set_settings_reuses_one_handle():
     assert ei.value.status == 1
     again = r.run(series[-1])           # still the last valid settings
     assert_same_measures(again, _oracle(settings[-1], series[-1])["measures"])
+    r.close()
+
+
+def test_served_stream_equals_single_runs():
+    """A Poisson stream with the served workload's lengths (1,000-200,000
+    points) and parameters, submitted on its arrival schedule: every result
+    equals the same series' single run (which the parity tests pin to the
+    oracle).  RQA_SERVE_TEST_SECONDS sets the stream's length (4 s; 60 s is
+    the measured workload's)."""
+    seconds = float(os.environ.get("RQA_SERVE_TEST_SECONDS", "4"))
+    arrivals, specs, series, eps = synth.serve_stream(rate=200.0, duration=seconds, seed=1105)
+    settings = [gp.Settings(m=sp.m, tau=sp.tau, eps=e, norm=sp.norm, theiler=sp.theiler,
+                            l_min=sp.l_min, v_min=sp.v_min, w_min=sp.w_min)
+                for sp, e in zip(specs, eps)]
+    srv = gp.Server(40 << 30, max_slots=64)
+    try:
+        t0 = time.perf_counter()
+        tickets = []
+        for at, stg, s in zip(arrivals, settings, series):
+            wait = at - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            tickets.append(srv.submit(stg, s))
+        got = []
+        for t in tickets:
+            rc, m = srv.wait(t, 120_000)
+            assert rc == 0
+            got.append(m)
+    finally:
+        srv.close()
+    r = gp.RQA(settings[0])
+    for q, (stg, s) in enumerate(zip(settings, series)):
+        r.set_settings(stg)
+        assert_same_measures(got[q], r.run(s))
     r.close()
