@@ -154,11 +154,37 @@ __device__ __forceinline__ void transpose32x2(uint32_t& x, uint32_t& z, int lane
 // and reported, never written.  A length outside 1..n is never counted; it
 // marks the series as failed instead.
 constexpr int OVF = 128;
+// Values of the current item that the hot loop uses rarely or once per row
+// block (descriptor pointers, the global histograms, the radius and band,
+// the recheck's FP64 inputs): one copy per CTA in shared memory, read at
+// each use with a volatile load so that the compiler keeps none of them in
+// registers across the loop.  At three CTAs per SM (80 registers a thread)
+// this leaves registers to the scans and the distance loop: 2.5 % faster on
+// the 1M-point L2 series than holding them in registers.
+struct StripCtx {
+  unsigned long long* gl;      // [3][nh+1]
+  unsigned long long* status;
+  uint32_t* colfirst;
+  uint16_t* rowA;              // row_a + the strip's row offset
+  uint16_t* rowZ;
+  uint16_t* dia_a;
+  uint16_t* dia_z;
+  int64_t dbase;               // descriptor of diagonal k: dbase + k (k >= klo)
+  const float* xe;
+  const double* sser;
+  double eps;
+  float thr, band;
+  int tau;
+  uint32_t nh;
+  int klo;
+  int mp;
+  const SeriesDesc* sp;
+};
+template <class V>
+__device__ __forceinline__ V ldv(const V& r) { return *reinterpret_cast<const volatile V*>(&r); }
 struct HistSink {
   uint32_t* sh;              // [3][HB]
-  unsigned long long* gl;    // [3][n+1]
-  uint32_t n;
-  unsigned long long* status;
+  const StripCtx* cx;
   uint32_t* q;               // this warp's queue: [1 + OVF]
   __device__ __forceinline__ void add(int type, uint32_t len) const {
     if (len - 1u < (uint32_t)(HB - 1)) {
@@ -174,6 +200,9 @@ struct HistSink {
     const uint32_t cnt = *reinterpret_cast<volatile uint32_t*>(q);
     if (cnt == 0) return;  // the same value in every lane
     const uint32_t m = cnt < (uint32_t)OVF ? cnt : (uint32_t)OVF;
+    unsigned long long* const gl = ldv(cx->gl);
+    unsigned long long* const status = ldv(cx->status);
+    const uint32_t n = ldv(cx->nh);
     for (uint32_t k = lane; k < m; k += 32) {
       const uint32_t v = q[1 + k], type = v >> 30, len = v & 0x3FFFFFFFu;
       if (len > 0 && len <= n)
@@ -534,6 +563,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
   __shared__ int s_item;
   __shared__ int s_skip;
   __shared__ volatile int s_abort;
+  __shared__ StripCtx s_ctx;
 
   // per-lane diagonal segment masks (lane d: lower segment bits d-1..0)
   const uint32_t segL = lowmask(lane);
@@ -556,7 +586,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
     const int it = s_item;
     if (it >= nitems) break;
     if (s_skip) continue;  // the series already failed (non-finite input or timeout)
-    unsigned long long rechecks = 0;
+    uint32_t rechecks = 0;  // per lane: at most C columns x n rows < 2^25 pairs
     const Item wi = items[it];
     const SeriesDesc* Sp = sd + wi.series;
     const int n = (int)Sp->n;                    // rows
@@ -596,7 +626,28 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
     const int wl_geo = XR ? (J1 - 1) / (32 * C) : (J1 - 2 - R0) / (32 * C);
     const int wlast = wl_geo < NW - 1 ? wl_geo : NW - 1;
     const int nh = XR ? (int)Sp->hl : n;             // longest possible line
-    const HistSink hs{sh_hist, Sp->hist, (uint32_t)nh, &Sp->counters[CNT_STATUS], ovfq};
+    if (threadIdx.x == 0) {
+      s_ctx.gl = Sp->hist;
+      s_ctx.status = &Sp->counters[CNT_STATUS];
+      s_ctx.colfirst = banded ? Sp->col_a + (int64_t)g * (XR ? ncol : n) : colend;
+      s_ctx.rowA = row_a + roff;
+      s_ctx.rowZ = row_z + roff;
+      s_ctx.dia_a = dia_a;
+      s_ctx.dia_z = dia_z;
+      s_ctx.dbase = off - klo;
+      s_ctx.xe = xe;
+      s_ctx.sser = sser;
+      s_ctx.nh = (uint32_t)nh;
+      s_ctx.klo = klo;
+      s_ctx.eps = eps;
+      s_ctx.thr = Sp->thr;
+      s_ctx.band = Sp->band;
+      s_ctx.tau = tau;
+      s_ctx.mp = mp;
+      s_ctx.sp = Sp;
+    }
+    __syncthreads();
+    const HistSink hs{sh_hist, &s_ctx, ovfq};
 
     if (warp <= wlast) {
       const bool leftmost = warp == wlast;
@@ -617,8 +668,6 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
       // first run of each column: next to the line of identity (colend), or
       // per band [nbands][columns], touching the band's bottom edge (or, for
       // RQA, the line of identity)
-      uint32_t* __restrict__ colfirst =
-          banded ? Sp->col_a + (int64_t)g * (XR ? ncol : n) : colend;
       uint32_t* ring_in = warp > 0 ? ring + (warp - 1) * RING * 64 : nullptr;
       uint32_t* ring_out = !leftmost ? ring + warp * RING * 64 : nullptr;
       int seq_in = 0, seq_out = 0;
@@ -656,19 +705,19 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
       int bufo = 0;  // which half of dU_s holds the carries of the block below
       ShortCounts sc{0, 0, 0, 0, 0};
       int since_flush = 0;
-      const float thr = Sp->thr;
-      const float band = Sp->band;
       bool ok = true;
 
       for (int b = bhi; b >= blo && ok; --b) {
         const int r0 = b << 5;
+        const float thr = ldv(s_ctx.thr);
+        const float band = ldv(s_ctx.band);
         if constexpr (!MX) {  // row vectors of rows r0 .. r0+31 into this warp's buffer
           const int i = r0 + lane;
           if constexpr (!F64) {
             // 16-byte loads of the padded FP32 vector (mp is a multiple of 4)
             // and 16-byte stores; the layout holds each coordinate twice.
             // Slots past the m coordinates are never read.
-            const float4* src = reinterpret_cast<const float4*>(xe + (int64_t)i * mp);
+            const float4* src = reinterpret_cast<const float4*>(ldv(s_ctx.xe) + (int64_t)i * ldv(s_ctx.mp));
             float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(rowbuf) + lane * RE);
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -860,9 +909,9 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
                 if (fabsf(acc) <= band) {
                   bool r;
                   if constexpr (XR)
-                    r = exact_decision2<NORM>(sser, sser2, r0 + t, j, M, tau, eps);
+                    r = exact_decision2<NORM>(sser, sser2, r0 + t, j, M, ldv(s_ctx.tau), ldv(s_ctx.eps));
                   else
-                    r = exact_decision<NORM>(sser, r0 + t, j, M, tau, eps);
+                    r = exact_decision<NORM>(ldv(s_ctx.sser), r0 + t, j, M, ldv(s_ctx.tau), ldv(s_ctx.eps));
                   R = r ? (R | (1u << t)) : (R & ~(1u << t));
                   ++rechecks;
                 }
@@ -943,14 +992,14 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
               cst_s[c * 32 + lane] = scan2_full(
                   R, cst_s[c * 32 + lane], sc, hs, emit2, [&](uint32_t col, uint32_t len) {
                     if (banded && R1 < n)  // touches the band's bottom edge: join later
-                      colfirst[j] = len | (col << 31);
+                      ldv(s_ctx.colfirst)[j] = len | (col << 31);
                     else if (len)
                       hs.add2(col, len);
                   });
               const int k = col0 - r0 + d;
               auto emitd = [&](uint32_t len) { hs.add(HIST_DIAG, len); };
               auto firstd = [&](uint32_t len) {
-                if (k >= klo) dia_a[off + k - klo] = (uint16_t)len;
+                if (k >= ldv(s_ctx.klo)) ldv(s_ctx.dia_a)[ldv(s_ctx.dbase) + k] = (uint16_t)len;
               };
               if (c == C - 1) {
                 dU_new[c * 32 + lane] =
@@ -974,14 +1023,14 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
               auto emit2 = [&](uint32_t col, uint32_t len) { hs.add2(col, len); };
               cst_s[c * 32 + lane] = scan2_full(
                   R, cst_s[c * 32 + lane], sc, hs, emit2,
-                  [&](uint32_t col, uint32_t len) { colfirst[j] = len | (col << 31); });
+                  [&](uint32_t col, uint32_t len) { ldv(s_ctx.colfirst)[j] = len | (col << 31); });
               rst = scan2_full(RW, rst, sc, hs, emit2, [&](uint32_t col, uint32_t len) {
-                row_a[roff + irow] = (uint16_t)((len << 1) | col);
+                ldv(s_ctx.rowA)[irow] = (uint16_t)((len << 1) | col);
               });
               const int k = col0 - r0 + d;
               auto emitd = [&](uint32_t len) { hs.add(HIST_DIAG, len); };
               auto firstd = [&](uint32_t len) {
-                if (k >= klo) dia_a[off + k - klo] = (uint16_t)len;
+                if (k >= ldv(s_ctx.klo)) ldv(s_ctx.dia_a)[ldv(s_ctx.dbase) + k] = (uint16_t)len;
               };
               if (c == C - 1) {
                 dU_new[c * 32 + lane] =
@@ -1005,11 +1054,11 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             auto firstc = [&](uint32_t col, uint32_t len) {
               if constexpr (XR) {
                 if (banded && R1 < n)  // touches the band's bottom edge: join later
-                  colfirst[j] = len | (col << 31);
+                  ldv(s_ctx.colfirst)[j] = len | (col << 31);
                 else if (len)
                   hs.add2(col, len);
               } else {
-                colfirst[j] = len | (col << 31);
+                ldv(s_ctx.colfirst)[j] = len | (col << 31);
               }
             };
             if (vt == 32)
@@ -1024,7 +1073,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             if (lo <= 31 && !(rst & ST_DONE) && row_valid) {
               auto emitr = [&](uint32_t col, uint32_t len) { hs.add2(col, len); };
               auto firstr = [&](uint32_t col, uint32_t len) {
-                row_a[roff + irow] = (uint16_t)((len << 1) | col);
+                ldv(s_ctx.rowA)[irow] = (uint16_t)((len << 1) | col);
               };
               if (lo <= 0)
                 rst = scan2_full(RW, rst, sc, hs, emitr, firstr);
@@ -1033,8 +1082,8 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
               if (lo >= 0) {  // the row ends here, at column irow + 1
                 const uint32_t len = rst & ST_LEN, col = (rst >> 28) & 1u;
                 const uint32_t same = (rst >> 29) & 1u;
-                row_z[roff + irow] = (uint16_t)((len << 2) | (same << 1) | col);
-                if (same) row_a[roff + irow] = 0;
+                ldv(s_ctx.rowZ)[irow] = (uint16_t)((len << 2) | (same << 1) | col);
+                if (same) ldv(s_ctx.rowA)[irow] = 0;
                 rst = ST_DONE;
               }
             }
@@ -1045,7 +1094,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             const int k = col0 - r0 + d;  // diagonal of this sub-block's upper segment
             auto emitd = [&](uint32_t len) { hs.add(HIST_DIAG, len); };
             auto firstd = [&](uint32_t len) {
-              if (k >= klo) dia_a[off + k - klo] = (uint16_t)len;
+              if (k >= ldv(s_ctx.klo)) ldv(s_ctx.dia_a)[ldv(s_ctx.dbase) + k] = (uint16_t)len;
             };
             if (c == C - 1) {
               // upper segment only (bits 31..d), entering from the right;
@@ -1073,7 +1122,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
                      (Dprev << (32 - d)) | lowmask(32 - d), du, sc, hs,
                      [&](uint32_t len) { hs.add(HIST_DIAG, len); },
                      [&](uint32_t len) {
-                       if (k >= klo) dia_a[off + k - klo] = (uint16_t)len;
+                       if (k >= ldv(s_ctx.klo)) ldv(s_ctx.dia_a)[ldv(s_ctx.dbase) + k] = (uint16_t)len;
                      }) -
                  (uint32_t)(32 - d);
           hs.drain(lane);
@@ -1090,13 +1139,13 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             const uint32_t len = rst & ST_LEN, col = (rst >> 28) & 1u;
             const uint32_t same = (rst >> 29) & 1u;
             if (len > 0) {
-              row_z[roff + irow] = (uint16_t)((len << 2) | (same << 1) | col);
-              if (same) row_a[roff + irow] = 0;
+              ldv(s_ctx.rowZ)[irow] = (uint16_t)((len << 2) | (same << 1) | col);
+              if (same) ldv(s_ctx.rowA)[irow] = 0;
             }
           }
           const int kx = jw0 - r0 + lane - 32;  // diagonal leaving through the left edge
-          if (kx >= klo)
-            dia_z[off + kx - klo] = (uint16_t)((dL & ST_LEN) | ((dL & DG_EDGE) ? 0x8000u : 0u));
+          if (kx >= ldv(s_ctx.klo))
+            ldv(s_ctx.dia_z)[ldv(s_ctx.dbase) + kx] = (uint16_t)((dL & ST_LEN) | ((dL & DG_EDGE) ? 0x8000u : 0u));
         } else if (b <= bhi_left) {
           if (lane == 0)
             ok = spin_until_ge(cons + (warp + 1), seq_out - RING + 1, &s_abort, spin_limit);
@@ -1110,7 +1159,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
           // test instantiation: from the chosen hand-over on, this warp stops
           // publishing, and the next warp's bounded wait gives up
           const bool withhold =
-              TW && warp + 1 == Sp->withhold_warp && seq_out + 1 >= Sp->withhold_seq;
+              TW && warp + 1 == ldv(s_ctx.sp)->withhold_warp && seq_out + 1 >= ldv(s_ctx.sp)->withhold_seq;
           if (lane == 0 && !withhold) prod[warp] = seq_out + 1;
           ++seq_out;
         }
@@ -1131,16 +1180,16 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
             if (!keep) {
               if (len > 0) {
                 if (!XR && whole)
-                  colfirst[j] = len | (col << 31);
+                  ldv(s_ctx.colfirst)[j] = len | (col << 31);
                 else
                   hs.add2(col, len);
               }
             } else {
-              Sp->col_z[(int64_t)g * (XR ? ncol : n) + j] =
+              ldv(s_ctx.sp)->col_z[(int64_t)g * (XR ? ncol : n) + j] =
                   len | (whole ? (1u << 30) : 0u) | (col << 31);
             }
             const uint32_t du = dU_s[bufo * C * 32 + c * 32 + lane];
-            dia_z[off + (j - R0) - klo] =
+            ldv(s_ctx.dia_z)[ldv(s_ctx.dbase) + (j - R0)] =
                 (uint16_t)((du & ST_LEN) | ((du & DG_EDGE) ? 0x8000u : 0u));
           }
         }
@@ -1149,18 +1198,19 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
       flush_short(sc, sh_hist, lane);
     }
     __syncthreads();
+    const SeriesDesc* const Sq = ldv(s_ctx.sp);
     if (s_abort && threadIdx.x == 0)
-      atomicCAS(&Sp->counters[CNT_STATUS], 0ull, 6ull /* RQA_ETIMEOUT */);
+      atomicCAS(&Sq->counters[CNT_STATUS], 0ull, 6ull /* RQA_ETIMEOUT */);
     // flush the strip's histograms
-    const int64_t stride = (int64_t)(XR ? (int)Sp->hl : n) + 1;
+    const int64_t stride = (int64_t)(XR ? (int)Sq->hl : n) + 1;
     for (int q = threadIdx.x; q < 3 * HB; q += blockDim.x) {
       const uint32_t v = sh_hist[q];
-      if (v) atomicAdd(&Sp->hist[(q / HB) * stride + (q % HB)], (unsigned long long)v);
+      if (v) atomicAdd(&Sq->hist[(q / HB) * stride + (q % HB)], (unsigned long long)v);
     }
     // rechecks of this strip: one atomic per warp
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rechecks += __shfl_xor_sync(FULL, rechecks, o);
-    if (lane == 0 && rechecks) atomicAdd(&Sp->counters[CNT_RECHECKS], rechecks);
+    if (lane == 0 && rechecks) atomicAdd(&Sq->counters[CNT_RECHECKS], (unsigned long long)rechecks);
   }
 }
 
