@@ -172,6 +172,7 @@ struct StripCtx {
   int64_t dbase;               // descriptor of diagonal k: dbase + k (k >= klo)
   const float* xe;
   const double* sser;
+  const double* sser2;         // cross recurrence: the column series
   double eps;
   float thr, band;
   int tau;
@@ -637,6 +638,7 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
       s_ctx.dbase = off - klo;
       s_ctx.xe = xe;
       s_ctx.sser = sser;
+      s_ctx.sser2 = sser2;
       s_ctx.nh = (uint32_t)nh;
       s_ctx.klo = klo;
       s_ctx.eps = eps;
@@ -909,7 +911,8 @@ tile_kernel(const SeriesDesc* __restrict__ sd, const Item* __restrict__ items, i
                 if (fabsf(acc) <= band) {
                   bool r;
                   if constexpr (XR)
-                    r = exact_decision2<NORM>(sser, sser2, r0 + t, j, M, ldv(s_ctx.tau), ldv(s_ctx.eps));
+                    r = exact_decision2<NORM>(ldv(s_ctx.sser), ldv(s_ctx.sser2), r0 + t, j, M, ldv(s_ctx.tau),
+                                             ldv(s_ctx.eps));
                   else
                     r = exact_decision<NORM>(ldv(s_ctx.sser), r0 + t, j, M, ldv(s_ctx.tau), ldv(s_ctx.eps));
                   R = r ? (R | (1u << t)) : (R & ~(1u << t));
